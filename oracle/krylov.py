@@ -1,0 +1,64 @@
+"""Restarted, right-preconditioned GCR (oracle).
+
+Test infrastructure only.  The paper solves the mixed system with GCR (Sec. 4.1 solver
+list; Sec. 5.1, outer tolerance 1e-6, following Melvin et al. 2018) and uses the same
+solver framework K(A, P, eps) for the pressure system (Eq. solver_notation).  The paper
+does not print the GCR recurrences; this is the textbook generalised conjugate residual
+method (Eisenstat, Elman & Schultz 1983) with right preconditioning and restart after
+``restart`` directions:
+
+    x = 0, r = b
+    repeat:  z = P r,  w = A z
+             for each stored (z_j, w_j):  beta = <w, w_j>/<w_j, w_j>,
+                                          w -= beta w_j,  z -= beta z_j   (modified G-S)
+             alpha = <r, w>/<w, w>,  x += alpha z,  r -= alpha w
+             store (z, w); clear the store after ``restart`` directions
+    until ||r||_2 <= tol ||b||_2.
+
+The recursively updated r is the true residual in exact arithmetic; ``gcr`` also
+returns the history of ||r|| / ||b||.
+"""
+from __future__ import annotations
+
+from typing import Callable
+
+import numpy as np
+
+
+def gcr(A: Callable, b: np.ndarray, P: Callable | None = None, tol: float = 1e-8,
+        restart: int = 5, maxiter: int = 500):
+    """Solve A x = b; returns (x, iterations, relative residual history)."""
+    b = np.asarray(b, dtype=np.float64).ravel()
+    P = (lambda v: v) if P is None else P
+    x = np.zeros_like(b)
+    r = b.copy()
+    nb = np.linalg.norm(b)
+    hist = [1.0]
+    if nb == 0.0:
+        return x, 0, hist
+    Z, W, WW = [], [], []
+    it = 0
+    while it < maxiter:
+        z = np.asarray(P(r), dtype=np.float64).ravel().copy()
+        w = np.asarray(A(z), dtype=np.float64).ravel().copy()
+        for zj, wj, wwj in zip(Z, W, WW):
+            beta = np.dot(w, wj) / wwj
+            w -= beta * wj
+            z -= beta * zj
+        ww = np.dot(w, w)
+        if not np.isfinite(ww) or ww == 0.0:
+            raise FloatingPointError("GCR breakdown: <w, w> = %r" % ww)
+        alpha = np.dot(r, w) / ww
+        x += alpha * z
+        r -= alpha * w
+        it += 1
+        hist.append(np.linalg.norm(r) / nb)
+        if hist[-1] <= tol:
+            break
+        if len(Z) + 1 >= restart:
+            Z, W, WW = [], [], []
+        else:
+            Z.append(z)
+            W.append(w)
+            WW.append(ww)
+    return x, it, hist

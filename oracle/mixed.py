@@ -1,0 +1,125 @@
+"""Reduced mixed (velocity, pressure) system and its Schur-complement preconditioner (oracle).
+
+Test infrastructure only.  Follows Maynard, Melvin & Mueller (arXiv 2002.00756):
+
+* Sec. 3.3, Eq. linear_matrix: the quasi-Newton linear system couples velocity u (faces,
+  RT0 at lowest order), density, potential temperature and pressure.  After the
+  elimination of theta (Step 1a, Eq. eliminate_theta) the velocity block becomes
+  M2-bar = M2 + P M_theta^{-1} P^z, whose extra term acts on vertical velocity only;
+  after the elimination of rho (Step 1b) a 2x2 (u, p) system remains.  The reduced
+  lowest-order system used here is, in strong volume-normalised form,
+
+      velocity row f:  (M-bar u)_f + (kappa_f / d_f) (p_R(f) - p_L(f)) = r_u,f
+      pressure row i:  p_i + (1 / V_i) sum_f sigma_if A_f u_f        = r_p,i
+
+  with kappa_f = (c_s dt)^2 g_f, sigma_if = +1 when the face normal points out of cell
+  i.  M-bar = I + eps B_w, where B_w couples each interior vertical face to the interior
+  vertical faces directly above (weight beta_up) and below (beta_dn) in its column
+  (non-symmetric, the folded buoyancy term of Step 1a).  The top and bottom faces carry
+  no flux: their rows are identity rows and they do not enter D or G.
+* Sec. 3.4: lumping M-bar to its row sums (diagonal M-ring) gives the Schur-complement
+  preconditioner, Steps 1-3:
+      B   = r_p - D M-ring^{-1} r_u                         (Eq. helmholtz right side)
+      Pi' ~ H^{-1} B,  H = I - D M-ring^{-1} G             (Eq. helmholtz_operator)
+      u'  = M-ring^{-1} (r_u - G Pi')                      (Eq. eliminate_u)
+  H is the Helmholtz operator of ``helmholtz.Level`` with the vertical coefficients
+  scaled by mu_f = 1 / M-ring_f.
+
+Velocity vector layout (the library's convention): [u_h, u_v]; u_h is (nlev, 2 ncol)
+level-major over the horizontal faces of ``Mesh.hfaces`` order; u_v is (nlev+1, ncol),
+face kf lying between cells kf-1 (below) and kf (above), kf = 0 and nlev the boundary.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+from .geometry import Mesh
+
+
+class MixedSystem:
+    def __init__(self, mesh: Mesh, g: np.ndarray, cs_dt: float, beta_up: np.ndarray,
+                 beta_dn: np.ndarray, eps: float):
+        self.mesh = mesh
+        nlev, ncol = mesh.nlev, mesh.ncol
+        self.nlev, self.ncol = nlev, ncol
+        g = np.asarray(g, dtype=np.float64).reshape(nlev, ncol)
+        c2 = cs_dt * cs_dt
+        self.L, self.R, side = mesh.hfaces()
+        self.nhf = len(self.L)
+        self.nh = nlev * self.nhf
+        self.nv = (nlev + 1) * ncol
+        self.nu = self.nh + self.nv
+        self.np = nlev * ncol
+        ell = mesh.edge_len[side, self.L]
+        dist = mesh.centre_dist[side, self.L]
+        # gradient weights kappa_f / d_f and divergence weights A_f / V_i
+        self.kd_h = c2 * 0.5 * (g[:, self.L] + g[:, self.R]) / dist[None, :]   # (nlev, nhf)
+        self.div_hL = ell / mesh.area[self.L]                                 # (nhf,)
+        self.div_hR = ell / mesh.area[self.R]
+        self.kd_v = np.zeros((nlev + 1, ncol))
+        for kf in range(1, nlev):
+            self.kd_v[kf] = c2 * 0.5 * (g[kf - 1] + g[kf]) / mesh.dzc[kf]
+        # velocity mass M-bar = I + eps B_w on vertical faces; couplings only between
+        # interior faces of the same column
+        interior = np.zeros(nlev + 1, dtype=bool)
+        interior[1:nlev] = True
+        up_ok = interior.copy()
+        up_ok[nlev - 1:] = False        # face kf couples to kf+1 only if kf+1 is interior
+        dn_ok = interior.copy()
+        dn_ok[:2] = False               # face kf couples to kf-1 only if kf-1 is interior
+        self.w_up = eps * np.asarray(beta_up, dtype=np.float64).reshape(nlev + 1, ncol) * up_ok[:, None]
+        self.w_dn = eps * np.asarray(beta_dn, dtype=np.float64).reshape(nlev + 1, ncol) * dn_ok[:, None]
+        self.m_lump = 1.0 + self.w_up + self.w_dn                            # row sums (Sec. 3.4)
+        self.mu = 1.0 / self.m_lump                                           # (nlev+1, ncol)
+
+    # ---- blocks ----
+    def split(self, v: np.ndarray):
+        v = np.asarray(v, dtype=np.float64).ravel()
+        u, p = v[: self.nu], v[self.nu:]
+        return (u[: self.nh].reshape(self.nlev, self.nhf), u[self.nh:].reshape(self.nlev + 1, self.ncol),
+                p.reshape(self.nlev, self.ncol))
+
+    def join(self, uh, uv, p) -> np.ndarray:
+        return np.concatenate([uh.ravel(), uv.ravel(), p.ravel()])
+
+    def grad(self, p: np.ndarray):
+        """G p on faces: (kappa_f / d_f)(p_R - p_L); zero on the boundary faces."""
+        p = p.reshape(self.nlev, self.ncol)
+        gh = self.kd_h * (p[:, self.R] - p[:, self.L])
+        gv = np.zeros((self.nlev + 1, self.ncol))
+        gv[1:self.nlev] = self.kd_v[1:self.nlev] * (p[1:] - p[:-1])
+        return gh, gv
+
+    def div(self, uh: np.ndarray, uv: np.ndarray) -> np.ndarray:
+        """D u in cells: (1 / V_i) sum_f sigma_if A_f u_f over the interior faces."""
+        out = np.zeros((self.nlev, self.ncol))
+        np.add.at(out, (slice(None), self.L), self.div_hL[None, :] * uh)
+        np.add.at(out, (slice(None), self.R), -self.div_hR[None, :] * uh)
+        rdz = 1.0 / self.mesh.dz
+        out[:-1] += rdz[:-1, None] * uv[1:self.nlev]      # top face of cell k (faces 1..nlev-1)
+        out[1:] -= rdz[1:, None] * uv[1:self.nlev]        # bottom face of cell k (faces 1..nlev-1)
+        return out
+
+    def mass(self, uv: np.ndarray) -> np.ndarray:
+        """M-bar on vertical faces (horizontal faces: identity)."""
+        y = uv.copy()
+        y[:-1] += self.w_up[:-1] * uv[1:]
+        y[1:] += self.w_dn[1:] * uv[:-1]
+        return y
+
+    # ---- operator and preconditioner ----
+    def apply(self, v: np.ndarray) -> np.ndarray:
+        """A_mixed [u; p] (Eq. linear_matrix, reduced lowest-order form)."""
+        uh, uv, p = self.split(v)
+        gh, gv = self.grad(p)
+        return self.join(uh + gh, self.mass(uv) + gv, p + self.div(uh, uv))
+
+    def precond(self, v: np.ndarray, helmholtz_solve) -> np.ndarray:
+        """Approximate Schur complement (Sec. 3.4, Steps 1-3) with a given H^{-1}."""
+        ruh, ruv, rp = self.split(v)
+        B = rp - self.div(ruh, ruv / self.m_lump)              # Step 1 (horizontal mass is 1)
+        pi = np.asarray(helmholtz_solve(B), dtype=np.float64).reshape(self.nlev, self.ncol)  # Step 2
+        gh, gv = self.grad(pi)
+        uh = ruh - gh                                            # Step 3
+        uv = (ruv - gv) / self.m_lump
+        return self.join(uh, uv, pi)

@@ -1,0 +1,96 @@
+"""Assembled matrices and direct solves: the plain definition of the solutions (oracle).
+
+Test infrastructure only.  ``pressure_solve`` and ``mixed_solve`` approximate the
+solution of a linear system (Eq. helmholtz and Eq. linear_matrix of Maynard, Melvin &
+Mueller, arXiv 2002.00756).  The reference solution x* is that of the assembled sparse
+matrix: by sparse LU (scipy.sparse.linalg.spsolve) or dense LU on small problems, and
+otherwise by the oracle's GCR to a relative residual of 1e-12 measured with the
+assembled matrix itself, so that x* does not depend on the matrix-free code it checks.
+"""
+from __future__ import annotations
+
+import numpy as np
+import scipy.sparse as sp
+import scipy.sparse.linalg as spla
+
+from .helmholtz import Level
+from .krylov import gcr
+from .mixed import MixedSystem
+
+
+def assemble_helmholtz(H: Level) -> sp.csr_matrix:
+    """H as a sparse matrix, row i = k * ncol + c, entry by entry from the coefficients."""
+    nlev, ncol = H.shape
+    N = nlev * ncol
+    idx = np.arange(N).reshape(nlev, ncol)
+    rows, cols, vals = [idx.ravel()], [idx.ravel()], [H.diag().ravel()]
+    for d in range(4):
+        rows.append(idx.ravel())
+        cols.append(idx[:, H.mesh.nbr[d]].ravel())
+        vals.append(-H.a_h[d].ravel())
+    rows.append(idx[:-1].ravel())
+    cols.append(idx[1:].ravel())
+    vals.append(-H.a_up[:-1].ravel())
+    rows.append(idx[1:].ravel())
+    cols.append(idx[:-1].ravel())
+    vals.append(-H.a_dn[1:].ravel())
+    return sp.csr_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))),
+                         shape=(N, N))
+
+
+def assemble_mixed(S: MixedSystem) -> sp.csr_matrix:
+    """[[M-bar, G], [D, I]] as one sparse matrix over [u_h, u_v, p]."""
+    nlev, ncol, nhf = S.nlev, S.ncol, S.nhf
+    rows, cols, vals = [], [], []
+
+    def put(r, c, v):
+        r, c, v = np.broadcast_arrays(r, c, v)
+        rows.append(r.ravel())
+        cols.append(c.ravel())
+        vals.append(v.ravel())
+
+    uh = np.arange(S.nh).reshape(nlev, nhf)
+    uv = S.nh + np.arange(S.nv).reshape(nlev + 1, ncol)
+    pp = S.nu + np.arange(S.np).reshape(nlev, ncol)
+    # velocity rows: horizontal faces
+    put(uh, uh, 1.0)
+    put(uh, pp[:, S.R], S.kd_h)
+    put(uh, pp[:, S.L], -S.kd_h)
+    # velocity rows: vertical faces
+    put(uv, uv, 1.0)
+    put(uv[:-1], uv[1:], S.w_up[:-1])
+    put(uv[1:], uv[:-1], S.w_dn[1:])
+    put(uv[1:nlev], pp[1:], S.kd_v[1:nlev])
+    put(uv[1:nlev], pp[:-1], -S.kd_v[1:nlev])
+    # pressure rows
+    put(pp, pp, 1.0)
+    put(pp[:, S.L], uh, S.div_hL[None, :])
+    put(pp[:, S.R], uh, -S.div_hR[None, :])
+    rdz = 1.0 / S.mesh.dz
+    put(pp[:-1], uv[1:nlev], rdz[:-1, None])
+    put(pp[1:], uv[1:nlev], -rdz[1:, None])
+    n = S.nu + S.np
+    A = sp.coo_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))),
+                      shape=(n, n))
+    A = A.tocsr()
+    A.eliminate_zeros()
+    return A
+
+
+def direct_solve(A: sp.spmatrix, b: np.ndarray) -> np.ndarray:
+    """Sparse LU solve (dense LU below 3000 unknowns)."""
+    b = np.asarray(b, dtype=np.float64).ravel()
+    if A.shape[0] <= 3000:
+        return np.linalg.solve(A.toarray(), b)
+    return spla.spsolve(A.tocsc(), b)
+
+
+def iterative_reference(A: sp.spmatrix, b: np.ndarray, P, tol: float = 1e-12,
+                        maxiter: int = 400) -> np.ndarray:
+    """GCR on the assembled matrix to a relative residual ``tol`` (checked again at the end)."""
+    b = np.asarray(b, dtype=np.float64).ravel()
+    x, _, _ = gcr(lambda v: A @ v, b, P, tol=tol, restart=20, maxiter=maxiter)
+    res = np.linalg.norm(b - A @ x) / np.linalg.norm(b)
+    if res > 10 * tol:
+        raise RuntimeError(f"reference solve reached only {res:.3e}")
+    return x

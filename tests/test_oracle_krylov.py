@@ -1,0 +1,72 @@
+"""Pins of the oracle's GCR against the minimal-residual definition and direct solves."""
+import numpy as np
+import pytest
+
+import synthetic as syn
+from oracle.krylov import gcr
+from oracle.multigrid import Hierarchy
+from oracle.reference import assemble_helmholtz, direct_solve
+
+R = 6371.0e3
+CSDT = 340.0 * 600.0
+
+
+def _nonsym(n=40, seed=0):
+    rng = np.random.default_rng(seed)
+    return np.eye(n) * 4 + rng.standard_normal((n, n)) * 0.4, rng.standard_normal(n)
+
+
+def _min_residual(A, b, P, k):
+    """min ||b - A x|| over x in P K_k(A P, b), from an orthonormal Krylov basis."""
+    AP = A @ P
+    K = np.empty((len(b), k))
+    v = b.copy()
+    for j in range(k):
+        K[:, j] = v
+        v = AP @ v
+    Q, _ = np.linalg.qr(K)
+    y, *_ = np.linalg.lstsq(AP @ Q, b, rcond=None)
+    return np.linalg.norm(b - AP @ Q @ y) / np.linalg.norm(b)
+
+
+@pytest.mark.parametrize("precond", [False, True])
+def test_unrestarted_gcr_is_minimal_residual(precond):
+    A, b = _nonsym()
+    P = np.diag(1.0 / np.diag(A)) if precond else np.eye(len(b))
+    _, _, hist = gcr(lambda v: A @ v, b, lambda r: P @ r, tol=1e-30, restart=1000, maxiter=8)
+    for k in range(1, 9):
+        assert hist[k] == pytest.approx(_min_residual(A, b, P, k), rel=1e-8)
+
+
+def test_restarted_gcr_residual_is_monotone_and_converges():
+    A, b = _nonsym(60, 1)
+    x, it, hist = gcr(lambda v: A @ v, b, None, tol=1e-10, restart=5, maxiter=400)
+    assert np.all(np.diff(hist) <= 1e-15)
+    assert np.linalg.norm(b - A @ x) / np.linalg.norm(b) <= 1e-10
+    # a restart discards the directions: iteration 6 can no longer be the global minimum
+    _, _, h5 = gcr(lambda v: A @ v, b, None, tol=1e-30, restart=5, maxiter=6)
+    assert h5[6] >= _min_residual(A, b, np.eye(60), 6) * (1 - 1e-10)
+
+
+def test_exact_preconditioner_converges_in_one_iteration():
+    A, b = _nonsym(30, 2)
+    Ainv = np.linalg.inv(A)
+    _, it, hist = gcr(lambda v: A @ v, b, lambda r: Ainv @ r, tol=1e-12)
+    assert it == 1 and hist[-1] < 1e-12
+
+
+def test_mg_preconditioned_gcr_matches_direct_solve():
+    n, nlev = 4, 6
+    g = np.exp(0.1 * syn.normal(5, 1, nlev * 6 * n * n))
+    h = Hierarchy(n, syn.z_interfaces(nlev), R, 2, g, CSDT)
+    H = h.levels[0]
+    b = syn.normal(5, 2, nlev * 6 * n * n)
+    x, it, hist = gcr(H.apply, b, h.as_preconditioner(), tol=1e-12, restart=5)
+    xs = direct_solve(assemble_helmholtz(H), b)
+    assert np.linalg.norm(x - xs) <= 1e-10 * np.linalg.norm(xs)
+    assert np.all(np.diff(hist) <= 0)
+
+
+def test_breakdown_is_reported():
+    with pytest.raises(FloatingPointError):
+        gcr(lambda v: 0 * v, np.ones(4), None, tol=1e-8)
