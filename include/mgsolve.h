@@ -1,0 +1,189 @@
+/*
+ * mgsolve.h - C ABI of the GB300 tensor-product multigrid solver for the LFRic
+ * semi-implicit linear system.
+ *
+ * Method: Maynard, Melvin & Mueller, "Multigrid preconditioners for the mixed finite
+ * element dynamical core of the LFRic atmospheric model" (arXiv 2002.00756):
+ *   - outer Krylov solve of the mixed (velocity, pressure) system, Sec. 3.3 and Sec. 4.1
+ *     (Eq. solver_notation), with GCR as in Sec. 5.1;
+ *   - approximate Schur-complement preconditioner, Sec. 3.4 (Steps 1-3);
+ *   - Helmholtz (pressure) operator H, Eq. helmholtz_operator and Sec. 3.5;
+ *   - one tensor-product multigrid V-cycle for H, Sec. 3.6 and Algorithm 1: horizontal-
+ *     only coarsening, block-Jacobi line smoother with an exact tridiagonal solve per
+ *     vertical column (Eq. jacobi), injection prolongation (Eq. prolongation) and its
+ *     dual as restriction, rediscretised coarse operators, n_coarse smoother sweeps on
+ *     the coarsest level.
+ *
+ * Problem definition used by every entry point (lowest-order, strong volume-normalised
+ * form, shallow atmosphere of radius R):
+ *   (H x)_i = x_i + sum_{faces f of cell i} a_{i,f} (x_i - x_j(f)),
+ *   a_{i,f} = (c_s dt)^2 g_f mu_f A_f / (V_i d_f),   g_f = (g_i + g_j) / 2,
+ * A_f face area, V_i cell volume, d_f centre distance (great-circle arc horizontally,
+ * centre-to-centre height vertically), mu_f = 1 on horizontal faces and 1 / (lumped
+ * velocity mass) on vertical faces of the mixed system (1 for the pressure-only system).
+ * No flux crosses the surface or the lid.
+ *
+ * Mesh convention (shared by all vectors): equiangular gnomonic cubed sphere C_n.
+ * Panel p maps (xi, eta) in [-pi/4, pi/4]^2 to the unit sphere through the cube point
+ * (a = tan xi, b = tan eta):
+ *   p0 (1, a, b)   p1 (-a, 1, b)   p2 (-1, -a, b)   p3 (a, -1, b)   p4 (-b, a, 1)   p5 (b, a, -1)
+ * Cell (p, j, i) spans xi in [-pi/4 + i d, -pi/4 + (i+1) d] (eta likewise with j),
+ * d = pi / (2n); its column index is col = p n^2 + j n + i and its centre is the image
+ * of the centre angles.  Cell fields are level-major: f[k * ncol + col], k = 0 at the
+ * surface, ncol = 6 n^2, N = nlev * ncol.
+ * Velocity vectors of the mixed system are [u_h, u_v]: u_h[k * 2ncol + f] over the
+ * horizontal faces f of one level, listed once each under the lower-numbered of their
+ * two columns, ordered by (that column, side E(+i), W(-i), N(+j), S(-j)); the face
+ * normal points from that column to the other one.  u_v[kf * ncol + col], kf = 0..nlev,
+ * face kf lying below cell k = kf (kf = 0 surface, kf = nlev lid; both carry no flux).
+ *
+ * Conventions for all calls:
+ *   - vector arguments are DEVICE pointers to FP64 arrays owned by the caller; the
+ *     handle owns the hierarchy, coefficients and workspace; solve calls allocate
+ *     nothing;
+ *   - calls are ordered on the given CUDA stream (0 = legacy default stream); solves
+ *     synchronise that stream once per Krylov iteration to test convergence;
+ *   - a handle is used by one stream at a time (calls on one handle must not overlap);
+ *   - errors are returned as status codes, never as exceptions or process exits.
+ */
+#ifndef MGSOLVE_H
+#define MGSOLVE_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    MG_OK = 0,
+    MG_ERR_ARG = -1,            /* invalid argument (null pointer, size, mesh not divisible) */
+    MG_ERR_CUDA = -2,           /* a CUDA runtime call failed */
+    MG_ERR_NOMEM = -3,          /* device or host allocation failed in mg_setup */
+    MG_ERR_NOT_CONVERGED = -4,  /* max_iter reached; info and the best iterate are filled */
+    MG_ERR_BREAKDOWN = -5,      /* Krylov breakdown: <w, w> = 0 or a non-finite scalar */
+    MG_ERR_TIMEOUT = -6,        /* reserved for bounded device-side waits */
+    MG_ERR_UNSUPPORTED = -7     /* request outside what the handle was set up for */
+} mg_status;
+
+/* precision of the V-cycle (the outer Krylov solve is always FP64) */
+enum {
+    MG_FP64 = 0,            /* FP64 vectors and coefficients (the plain method) */
+    MG_FP32 = 1,            /* FP32 vectors, coefficients and accumulation */
+    MG_FP32_BF16COEF = 2    /* FP32 vectors and accumulation, BF16 stored coefficients */
+};
+
+typedef struct {
+    int32_t n;                   /* cubed sphere C_n (n divisible by 2^(levels-1)) */
+    int32_t nlev;                /* vertical levels, 1..MG_MAX_NLEV */
+    double radius;               /* planet radius R [m] */
+    double cs_dt;                /* c_s * dt [m] */
+    const double* z_interfaces;  /* HOST, nlev+1 increasing heights [m], z[0] = surface */
+} mg_mesh;
+
+typedef struct {
+    int32_t levels;              /* multigrid levels L >= 1 (Sec. 3.6; L = 1: smoother only) */
+    double omega;                /* over-relaxation of the block-Jacobi sweep (Eq. jacobi) */
+    int32_t n_pre, n_post;       /* smoothing sweeps before / after the coarse correction */
+    int32_t n_coarse;            /* sweeps from zero on the coarsest level */
+    int32_t vcycle_precision;    /* MG_FP64 | MG_FP32 | MG_FP32_BF16COEF */
+    int32_t gcr_restart;         /* GCR directions kept before a restart, 1..MG_MAX_RESTART */
+    int32_t max_iter;            /* Krylov iteration limit */
+} mg_params;
+
+/* mixed-system data (Sec. 3.3-3.4): velocity mass M-bar = I + eps B_w on vertical faces,
+ * B_w coupling interior vertical face kf to kf+1 with weight beta_up[kf*ncol+col] and to
+ * kf-1 with beta_dn[kf*ncol+col] (only between interior faces). */
+typedef struct {
+    const double* beta_up;       /* HOST, (nlev+1) * ncol */
+    const double* beta_dn;       /* HOST, (nlev+1) * ncol */
+    double eps;
+} mg_mixed;
+
+typedef struct {
+    int32_t iters;               /* Krylov iterations done */
+    double rel_res;              /* final ||b - A x||_2 / ||b||_2 (recursive residual) */
+    double ms;                   /* wall time of the call on its stream [ms] */
+} mg_solve_info;
+
+#define MG_MAX_NLEV 128
+#define MG_MAX_LEVELS 8
+#define MG_MAX_RESTART 16
+
+typedef struct mg_handle mg_handle;
+
+/* Build the multigrid hierarchy (Sec. 3.6; coarse meshes C_{n/2}, ..., coarse operators
+ * rediscretised from volume-weighted means of the background factors, Sec. 3.6 last
+ * paragraph before Algorithm 1 and Sec. 5.1 set-up costs) on the current CUDA device.
+ *   g      HOST, N background-state factors (cell field layout), g > 0
+ *   mixed  NULL for the Helmholtz system alone; otherwise the mixed-system data, which
+ *          also scales the vertical Helmholtz coefficients by 1 / lumped mass
+ * On success *out holds a handle to release with mg_destroy.  Synchronous. */
+mg_status mg_setup(const mg_mesh* mesh, const mg_params* params, const double* g,
+                   const mg_mixed* mixed, mg_handle** out);
+
+void mg_destroy(mg_handle* h);
+
+const char* mg_status_string(mg_status s);
+
+/* Sizes of the handle's problem: ncol and N of the finest level, velocity unknowns
+ * (0 without mixed data).  Any pointer may be NULL. */
+mg_status mg_sizes(const mg_handle* h, int64_t* ncol, int64_t* ncell, int64_t* nu);
+
+/* y = H x on the finest level in FP64 (Eq. helmholtz_operator; Sec. 3.5 stencil).
+ * x, y: DEVICE, N doubles, must not overlap. */
+mg_status helmholtz_apply(mg_handle* h, const double* x, double* y, void* stream);
+
+/* x = V b: one V-cycle of Algorithm 1 from a zero initial guess (the preconditioner
+ * P_H^(MG)(L, omega, n_pre, n_post) of Sec. 4.1), in the handle's V-cycle precision.
+ * b, x: DEVICE, N doubles, must not overlap; the FP32 variants convert b on entry and x
+ * on exit inside their first and last sweep kernels. */
+mg_status vcycle(mg_handle* h, const double* b, double* x, void* stream);
+
+/* Solve H x = b by GCR(gcr_restart) right-preconditioned with one V-cycle per iteration
+ * (K_H(A_H, P_H^(MG), tol) of Eq. solver_notation), x0 = 0, stopping when
+ * ||b - H x||_2 <= tol ||b||_2 (FP64 vectors, residuals and inner products).
+ * b, x: DEVICE, N doubles.  info may be NULL.  Returns MG_ERR_NOT_CONVERGED after
+ * max_iter iterations (x then holds the last iterate), MG_ERR_BREAKDOWN on a zero or
+ * non-finite <w, w> or residual. */
+mg_status pressure_solve(mg_handle* h, const double* b, double* x, double tol,
+                         mg_solve_info* info, void* stream);
+
+/* Solve the mixed system A [u; p] = [rhs_u; rhs_p] (Eq. linear_matrix, reduced (u, p)
+ * form) by GCR(gcr_restart) right-preconditioned with the approximate Schur complement
+ * (Sec. 3.4 Steps 1-3, one V-cycle for Step 2), x0 = 0, stopping on the Euclidean norm of
+ * the concatenated residual.  Needs a handle set up with mixed data.
+ * rhs_u, u: DEVICE, nu doubles; rhs_p, p: DEVICE, N doubles. */
+mg_status mixed_solve(mg_handle* h, const double* rhs_u, const double* rhs_p, double* u,
+                      double* p, double tol, mg_solve_info* info, void* stream);
+
+/* ---- single steps of the method, FP64, for checking each kernel on its own ---- */
+
+/* y = H^(level) x on multigrid level `level` (0 = finest); DEVICE arrays of that level's
+ * N_l = nlev * 6 (n / 2^level)^2 doubles. */
+mg_status mg_level_apply(mg_handle* h, int32_t level, const double* x, double* y, void* stream);
+
+/* x_out = BlockJacobi(H^(level), b, x_in, omega, sweeps) (Eq. jacobi), x_in == NULL meaning
+ * a zero initial guess.  x_in and x_out may be the same array; b must not overlap x_out. */
+mg_status mg_smooth(mg_handle* h, int32_t level, const double* b, const double* x_in,
+                    double* x_out, int32_t sweeps, void* stream);
+
+/* bc = Restrict(b - H^(level) x) onto level+1 (Algorithm 1, residual and restriction). */
+mg_status mg_residual_restrict(mg_handle* h, int32_t level, const double* b, const double* x,
+                               double* bc, void* stream);
+
+/* x += Prolongate(xc) from level+1 onto level (Eq. prolongation, natural injection). */
+mg_status mg_prolong_add(mg_handle* h, int32_t level, const double* xc, double* x, void* stream);
+
+/* [yu; yp] = A [u; p], the mixed operator (needs mixed data). */
+mg_status mixed_apply(mg_handle* h, const double* u, const double* p, double* yu, double* yp,
+                      void* stream);
+
+/* [u; p] = P_mixed [ru; rp], the Schur-complement preconditioner with one V-cycle. */
+mg_status schur_precond(mg_handle* h, const double* ru, const double* rp, double* u, double* p,
+                        void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -85,9 +85,15 @@ class Level:
         return -self.a_dn, self.diag(), -self.a_up
 
     def hz_solve(self, r: np.ndarray) -> np.ndarray:
-        """H_z-hat^{-1} r, every column by the textbook Thomas algorithm."""
-        lower, diag, upper = self.hz_bands()
-        return thomas(lower, diag, upper, np.asarray(r, dtype=np.float64).reshape(self.shape))
+        """H_z-hat^{-1} r, every column by the Thomas algorithm (pivot-excess form).
+
+        The textbook recurrence loses about log10(CFL_v^2) digits on the vertically
+        smooth mode when the vertical coefficients reach 1e6-1e7; the excess form below is
+        the same elimination with every pivot kept as a sum of positive terms.
+        """
+        s = 1.0 + self.a_h.sum(axis=0)
+        return thomas_excess(self.a_dn, s, self.a_up,
+                             np.asarray(r, dtype=np.float64).reshape(self.shape))
 
     def jacobi(self, b: np.ndarray, x: np.ndarray, omega: float, sweeps: int) -> np.ndarray:
         """BlockJacobi(H, b, x, omega, sweeps): Eq. jacobi applied ``sweeps`` times."""
@@ -124,8 +130,8 @@ def thomas_excess(a_dn: np.ndarray, s: np.ndarray, a_up: np.ndarray, r: np.ndarr
     s_k = 1 + (horizontal coefficients) > 0, elimination gives
         q_0 = s_0,   q_k = s_k + a_dn_k q_{k-1} / p_{k-1},   p_k = q_k + a_up_k,
     so every pivot is a sum of positive terms (no cancellation between the O(1)
-    identity part and the O(CFL_v^2) vertical terms).  Used as an algebraic cross-check
-    of ``thomas``.
+    identity part and the O(CFL_v^2) vertical terms).  Forward sweep y_k = r_k +
+    (a_dn_k / p_{k-1}) y_{k-1}, back substitution x_k = (y_k + a_up_k x_{k+1}) / p_k.
     """
     n = s.shape[0]
     p = np.empty_like(s)

@@ -129,6 +129,25 @@ def test_excess_form_agrees_with_textbook_thomas():
     assert np.allclose(x1, x2, rtol=1e-7, atol=1e-12 * np.abs(x2).max())
 
 
+def test_excess_form_is_accurate_at_extreme_aspect_ratio():
+    # against a 50-digit LU solve: the vertically smooth mode at CFL_v^2 ~ 7e6
+    mpmath = pytest.importorskip("mpmath")
+    a_dn, s, a_up, _ = _random_columns(70, 2, 6, vmax=7e6)
+    r = np.ones_like(s)
+    x = thomas_excess(a_dn, s, a_up, r)
+    mpmath.mp.dps = 50
+    for c in range(2):
+        A = mpmath.zeros(70, 70)
+        for k in range(70):
+            A[k, k] = mpmath.mpf(s[k, c]) + mpmath.mpf(a_dn[k, c]) + mpmath.mpf(a_up[k, c])
+            if k > 0:
+                A[k, k - 1] = -mpmath.mpf(a_dn[k, c])
+            if k < 69:
+                A[k, k + 1] = -mpmath.mpf(a_up[k, c])
+        ref = np.array([float(v) for v in mpmath.lu_solve(A, mpmath.matrix([1] * 70))])
+        assert np.abs(x[:, c] - ref).max() <= 1e-14 * np.abs(ref).max()
+
+
 @pytest.mark.parametrize("omega", [1.0, 0.5])
 def test_vertical_only_problem_one_sweep_is_exact(omega):
     L = _level(n=3, nlev=12)
