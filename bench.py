@@ -1,0 +1,334 @@
+"""Benchmark: ms per pressure solve to 1e-8 relative residual at C192L70 on GB300.
+
+One step = one pressure solve H x = b (Eq. helmholtz) by FP64 GCR(5) right-preconditioned
+with one multigrid V-cycle per iteration (Algorithm 1, FP32 vectors and coefficients,
+FP32 accumulation), from x = 0 to ||b - H x|| <= 1e-8 ||b||, on the synthetic C192L70
+workload (221,184 columns x 70 levels = 15,482,880 unknowns, seeded inputs).
+
+Printed JSON line (rank 0):
+  value        ms per solve, inputs resident in HBM (whole job: timed region / solves done)
+  e2e          the same through the public API with host (pinned) buffers: H2D of b, the
+               solve, D2H of x inside every timed step
+  roofline     dominant kernel (finest-level block-Jacobi sweep): algorithmic bytes per launch
+               / event-timed launch duration, against the measured HBM copy bandwidth
+  cpu_baseline the CPU oracle (numpy FP64, as it stands) timed on a bounded sample
+  clocks       nvidia-smi samples taken during the timed region
+
+--impl reference times the CPU oracle (the reference of this build) on the same workload:
+one GCR iteration of the oracle's pressure solve per step.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import synthetic as syn  # noqa: E402
+
+METRIC = "ms per pressure solve to 1e-8 rel. residual at C192L70"
+UNIT = "ms"
+WORKLOAD = "C192L70 pressure solve: GCR(5) FP64 outer + 4-level FP32 V-cycle, tol 1e-8"
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, ValueError):
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        self.result = {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        if self.proc is None:
+            return
+        time.sleep(0.2)
+        self.proc.terminate()
+        out, _ = self.proc.communicate(timeout=10)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if sm:
+            self.result = {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                           "samples": len(sm)}
+
+
+def dist_init():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def cpu_oracle_iteration_time(cfg, inp, iters: int = 1):
+    """Seconds per GCR iteration of the oracle's pressure solve (setup excluded)."""
+    from oracle.krylov import gcr
+    from oracle.problem import pressure_hierarchy
+    hier = pressure_hierarchy(cfg, inp)
+    H = hier.levels[0]
+    P = hier.as_preconditioner(cfg.omega, cfg.n_pre, cfg.n_post, cfg.n_coarse)
+    t0 = time.perf_counter()
+    _, it, hist = gcr(H.apply, inp["rhs"], P, tol=0.0, restart=cfg.gcr_restart, maxiter=iters)
+    return (time.perf_counter() - t0) / it, hist
+
+
+def run_reference(args, cfg, inp, world, rank):
+    """CPU oracle arm: one oracle GCR iteration per step, solves restarted from x = 0."""
+    if rank != 0:
+        return
+    from oracle.problem import pressure_hierarchy
+    hier = pressure_hierarchy(cfg, inp)
+    H = hier.levels[0]
+    P = hier.as_preconditioner(cfg.omega, cfg.n_pre, cfg.n_post, cfg.n_coarse)
+    b = inp["rhs"]
+    nb = np.linalg.norm(b)
+    for _ in range(args.warmup):          # warm-up: one operator application each
+        H.apply(b)
+
+    class Solve:
+        def __init__(self):
+            self.x = np.zeros_like(b)
+            self.r = b.copy()
+            self.Z, self.W, self.WW = [], [], []
+
+        def step(self):
+            z = np.asarray(P(self.r)).ravel().copy()
+            w = H.apply(z).ravel()
+            for zj, wj, wwj in zip(self.Z, self.W, self.WW):
+                beta = np.dot(w, wj) / wwj
+                w -= beta * wj
+                z -= beta * zj
+            ww = np.dot(w, w)
+            a = np.dot(self.r, w) / ww
+            self.x += a * z
+            self.r -= a * w
+            if len(self.Z) + 1 >= cfg.gcr_restart:
+                self.Z, self.W, self.WW = [], [], []
+            else:
+                self.Z.append(z)
+                self.W.append(w)
+                self.WW.append(ww)
+            return np.linalg.norm(self.r) / nb
+
+    s = Solve()
+    its, times, per_solve_iters = 0, [], []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        rel = s.step()
+        times.append(time.perf_counter() - t0)
+        its += 1
+        if rel <= args.tol:
+            per_solve_iters.append(its)
+            its = 0
+            s = Solve()
+    sec_it = float(np.mean(times))
+    if per_solve_iters:
+        n_it = float(np.mean(per_solve_iters))
+        how = f"{len(per_solve_iters)} oracle solve(s) completed within the timed steps"
+    else:   # extrapolate the observed residual contraction to 1e-8
+        rho = rel ** (1.0 / its)
+        n_it = float(np.ceil(np.log(args.tol) / np.log(rho)))
+        how = f"iterations to 1e-8 extrapolated from {its} steps (mean contraction {rho:.3f})"
+    value = sec_it * n_it * 1e3
+    line = {
+        "impl": "reference", "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(sec_it * 1e3, 3),
+        "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": WORKLOAD.replace("FP32 V-cycle", "FP64 V-cycle (CPU oracle)"),
+                                        "n": cfg.n, "nlev": cfg.nlev, "levels": cfg.levels},
+        "cpu_baseline": {"value": round(value, 3), "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"one numpy FP64 GCR iteration of the C192L70 solve per step; "
+                                   f"ms/solve = mean iteration time x {n_it:.1f} iterations ({how})"},
+        "e2e": {"value": round(value, 3), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="c192")
+    ap.add_argument("--precision", default="fp32", choices=["fp64", "fp32", "fp32_bf16"])
+    ap.add_argument("--tol", type=float, default=1e-8)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "ours":
+        args.warmup = 3
+    world, rank, local = dist_init()
+    cfg = syn.config(args.workload)
+    inp = syn.make_inputs(cfg, mixed=False)
+    if args.impl == "reference":
+        return run_reference(args, cfg, inp, world, rank)
+
+    import torch
+    torch.cuda.set_device(local)
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+        pg = dist
+    from paper_2002_00756_gb300.build import build
+    if rank == 0:
+        build()
+    if pg:
+        pg.barrier()
+    import paper_2002_00756_gb300 as mg
+
+    h = mg.mg_setup_config(cfg, inp, precision=args.precision, mixed=False)
+    stream = torch.cuda.current_stream()
+    b = torch.from_numpy(inp["rhs"]).cuda()
+    x = torch.zeros_like(b)
+    for _ in range(args.warmup):
+        info = mg.pressure_solve(h, b, x, tol=args.tol)
+        assert info.converged, info
+    torch.cuda.synchronize()
+
+    # ---- timed region: K solves, inputs resident in HBM ----
+    mg.mg_profile_start(h, 1 << 18)
+    iters = []
+    with Clocks(local) as clk:
+        if pg:
+            pg.barrier()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            info = mg.pressure_solve(h, b, x, tol=args.tol)
+            iters.append(info.iters)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        if pg:
+            pg.barrier()
+    recs = mg.mg_profile_stop(h)
+    ms_total = e0.elapsed_time(e1)
+    if pg:
+        t = torch.tensor([ms_total], device="cuda")
+        pg.all_reduce(t, op=pg.ReduceOp.MAX)
+        ms_total = float(t.item())
+    ms_per_solve = ms_total / (args.steps * world)
+
+    # ---- e2e: host buffers through the public API ----
+    bh = torch.from_numpy(inp["rhs"]).pin_memory()
+    xh = torch.empty_like(bh).pin_memory()
+    bd = torch.empty_like(b)
+    xd = torch.empty_like(b)
+    e2e_steps = max(3, min(args.steps, 20))
+    torch.cuda.synchronize()
+    if pg:
+        pg.barrier()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        bd.copy_(bh, non_blocking=True)
+        mg.pressure_solve(h, bd, xd, tol=args.tol)
+        xh.copy_(xd, non_blocking=True)
+        torch.cuda.synchronize()
+    e2e_ms = (time.perf_counter() - t0) * 1e3
+    if pg:
+        t = torch.tensor([e2e_ms], device="cuda")
+        pg.all_reduce(t, op=pg.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+    e2e_ms /= (e2e_steps * world)
+
+    # ---- roofline of the dominant kernel (finest-level sweep) ----
+    peak, peak_src = _peaks()
+    by = {}
+    for r in recs:
+        k = (r["kind"], r["level"])
+        a = by.setdefault(k, [0, 0.0, 0.0])
+        a[0] += 1
+        a[1] += r["ms"]
+        a[2] += r["bytes"]
+    top = max(by.items(), key=lambda kv: kv[1][1])
+    (kind, lev), (cnt, ms, byt) = top
+    achieved = byt / (ms * 1e-3) / 1e9
+    vc_kinds = ("sweep", "restrict", "prolong", "convert")
+    vc_ms = sum(v[1] for k, v in by.items() if k[0] in vc_kinds)
+    vc_bytes = sum(v[2] for k, v in by.items() if k[0] in vc_kinds)
+    total_kernel_ms = sum(v[1] for v in by.values())
+    breakdown = {f"{k[0]}@L{k[1]}": {"launches": v[0], "ms": round(v[1], 3),
+                                     "share": round(v[1] / total_kernel_ms, 4),
+                                     "GBps": round(v[2] / (v[1] * 1e-3) / 1e9, 1)}
+                 for k, v in sorted(by.items(), key=lambda kv: -kv[1][1])}
+
+    line = {
+        "metric": METRIC, "value": round(ms_per_solve, 4), "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_total / args.steps, 4),
+        "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64" if args.precision == "fp64" else "f64+f32",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD if args.precision == "fp32" else WORKLOAD.replace("FP32", args.precision),
+                   "n": cfg.n, "nlev": cfg.nlev, "unknowns": cfg.ncell, "levels": cfg.levels,
+                   "vcycle_precision": args.precision, "tol": args.tol, "gcr_restart": cfg.gcr_restart,
+                   "iters_per_solve": statistics.mean(iters), "replicas": world,
+                   "l2": "working set (~3 GB) larger than L2; no flush"},
+        "e2e": {"value": round(e2e_ms, 4), "unit": UNIT, "h2d_bytes_per_step": int(b.numel() * 8),
+                "d2h_bytes_per_step": int(b.numel() * 8)},
+        "roofline": {"bound": "hbm", "kernel": f"{kind}@L{lev}", "achieved": round(achieved, 1), "peak": peak,
+                     "unit": "GB/s", "frac": round(achieved / peak, 4), "traffic": None,
+                     "peak_source": peak_src,
+                     "vcycle_GBps": round(vc_bytes / (vc_ms * 1e-3) / 1e9, 1),
+                     "vcycle_frac": round(vc_bytes / (vc_ms * 1e-3) / 1e9 / peak, 4)},
+        "gpu_launches": len(recs),
+        "kernels": breakdown,
+        "clocks": clk.result,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        sec_it, hist = cpu_oracle_iteration_time(cfg, inp, iters=1)
+        n_it = statistics.mean(iters)
+        line["cpu_baseline"] = {
+            "value": round(sec_it * n_it * 1e3, 1), "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"one numpy FP64 GCR iteration of the same C192L70 solve ({sec_it:.1f} s) x "
+                      f"{n_it:.1f} iterations per solve (the GPU solve's count)"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    h.destroy()
+    if pg:
+        pg.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -183,6 +183,37 @@ mg_status mixed_apply(mg_handle* h, const double* u, const double* p, double* yu
 mg_status schur_precond(mg_handle* h, const double* ru, const double* rp, double* u, double* p,
                         void* stream);
 
+/* ---- per-launch profiling ----
+ * While profiling is on, every kernel launch made by the calls above is bracketed by two
+ * CUDA events on its stream, and its kind, multigrid level and algorithmic traffic (every
+ * array element the kernel must read or write, counted once) are recorded. */
+enum {
+    MG_K_SWEEP = 0,       /* block-Jacobi sweep (residual + Thomas + update) */
+    MG_K_RESTRICT = 1,    /* residual + restriction */
+    MG_K_PROLONG = 2,     /* prolongation (when not fused into a sweep) */
+    MG_K_APPLY = 3,       /* Helmholtz apply */
+    MG_K_CONVERT = 4,     /* precision conversion */
+    MG_K_DOT = 5,         /* inner product */
+    MG_K_GCR_DOTS = 6,    /* GCR orthogonalisation inner products */
+    MG_K_GCR_ORTH = 7,    /* GCR orthogonalisation update + <w,w>, <r,w> */
+    MG_K_GCR_UPDATE = 8,  /* GCR x, r update + <r,r> */
+    MG_K_MIXED = 9        /* mixed operator / Schur steps */
+};
+
+typedef struct {
+    int32_t kind;      /* MG_K_* */
+    int32_t level;     /* multigrid level (0 = finest) */
+    double bytes;      /* algorithmic bytes of the launch */
+    double ms;         /* event-timed duration */
+} mg_kernel_record;
+
+/* Start recording up to `capacity` launches (creates the events; not a solve call). */
+mg_status mg_profile_start(mg_handle* h, int32_t capacity);
+
+/* Stop recording, synchronise the device and copy up to `cap` records to `out` (HOST);
+ * *count receives the number recorded (launches beyond the capacity are not timed). */
+mg_status mg_profile_stop(mg_handle* h, mg_kernel_record* out, int32_t cap, int32_t* count);
+
 #ifdef __cplusplus
 }
 #endif

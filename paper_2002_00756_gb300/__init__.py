@@ -1,0 +1,305 @@
+"""Python binding of libmgsolve.so, the GB300 column multigrid solver (C ABI in include/mgsolve.h).
+
+Argument marshalling only: every step of the solve runs in the library's CUDA kernels.
+Vectors are torch CUDA tensors of dtype float64 (contiguous); host inputs (background
+factors, level heights, mixed-system weights) are numpy arrays.  Calls are issued on the
+current torch CUDA stream unless a stream is given.
+
+The library must have been built (``paper_2002_00756_gb300.build.build()`` or
+``__graft_entry__.build()``); there is no fallback implementation.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+from .build import LIB as _LIB_PATH
+
+MG_OK, MG_ERR_ARG, MG_ERR_CUDA, MG_ERR_NOMEM = 0, -1, -2, -3
+MG_ERR_NOT_CONVERGED, MG_ERR_BREAKDOWN, MG_ERR_TIMEOUT, MG_ERR_UNSUPPORTED = -4, -5, -6, -7
+MG_FP64, MG_FP32, MG_FP32_BF16COEF = 0, 1, 2
+PRECISIONS = {"fp64": MG_FP64, "fp32": MG_FP32, "fp32_bf16": MG_FP32_BF16COEF}
+
+
+class MGError(RuntimeError):
+    def __init__(self, status: int, what: str):
+        self.status = status
+        super().__init__(f"{what}: {status_string(status)} ({status})")
+
+
+class _Mesh(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int32), ("nlev", ctypes.c_int32), ("radius", ctypes.c_double),
+                ("cs_dt", ctypes.c_double), ("z_interfaces", ctypes.POINTER(ctypes.c_double))]
+
+
+class _Params(ctypes.Structure):
+    _fields_ = [("levels", ctypes.c_int32), ("omega", ctypes.c_double), ("n_pre", ctypes.c_int32),
+                ("n_post", ctypes.c_int32), ("n_coarse", ctypes.c_int32),
+                ("vcycle_precision", ctypes.c_int32), ("gcr_restart", ctypes.c_int32),
+                ("max_iter", ctypes.c_int32)]
+
+
+class _Mixed(ctypes.Structure):
+    _fields_ = [("beta_up", ctypes.POINTER(ctypes.c_double)), ("beta_dn", ctypes.POINTER(ctypes.c_double)),
+                ("eps", ctypes.c_double)]
+
+
+class _KRec(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("level", ctypes.c_int32), ("bytes", ctypes.c_double),
+                ("ms", ctypes.c_double)]
+
+
+KERNEL_KINDS = ("sweep", "restrict", "prolong", "apply", "convert", "dot", "gcr_dots", "gcr_orth",
+                "gcr_update", "mixed")
+
+
+class _Info(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int32), ("rel_res", ctypes.c_double), ("ms", ctypes.c_double)]
+
+
+_lib = None
+
+_VP, _DP, _I32, _D = ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, ctypes.c_double
+_SIGS = {
+    "mg_setup": [ctypes.POINTER(_Mesh), ctypes.POINTER(_Params), ctypes.POINTER(ctypes.c_double),
+                 ctypes.POINTER(_Mixed), ctypes.POINTER(ctypes.c_void_p)],
+    "mg_destroy": [_VP],
+    "mg_sizes": [_VP, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)],
+    "helmholtz_apply": [_VP, _DP, _DP, _VP],
+    "vcycle": [_VP, _DP, _DP, _VP],
+    "pressure_solve": [_VP, _DP, _DP, _D, ctypes.POINTER(_Info), _VP],
+    "mixed_solve": [_VP, _DP, _DP, _DP, _DP, _D, ctypes.POINTER(_Info), _VP],
+    "mg_level_apply": [_VP, _I32, _DP, _DP, _VP],
+    "mg_smooth": [_VP, _I32, _DP, _DP, _DP, _I32, _VP],
+    "mg_residual_restrict": [_VP, _I32, _DP, _DP, _DP, _VP],
+    "mg_prolong_add": [_VP, _I32, _DP, _DP, _VP],
+    "mixed_apply": [_VP, _DP, _DP, _DP, _DP, _VP],
+    "schur_precond": [_VP, _DP, _DP, _DP, _DP, _VP],
+    "mg_profile_start": [_VP, _I32],
+    "mg_profile_stop": [_VP, ctypes.POINTER(_KRec), _I32, ctypes.POINTER(ctypes.c_int32)],
+}
+
+
+def library_path() -> str:
+    return _LIB_PATH
+
+
+def load() -> ctypes.CDLL:
+    """Load libmgsolve.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(_LIB_PATH):
+            raise ImportError(f"{_LIB_PATH} is missing: build it with paper_2002_00756_gb300.build.build()")
+        lib = ctypes.CDLL(_LIB_PATH)
+        for name, args in _SIGS.items():
+            fn = getattr(lib, name)
+            fn.argtypes = args
+            fn.restype = None if name == "mg_destroy" else ctypes.c_int
+        lib.mg_status_string.argtypes = [ctypes.c_int]
+        lib.mg_status_string.restype = ctypes.c_char_p
+        _lib = lib
+    return _lib
+
+
+def status_string(status: int) -> str:
+    return load().mg_status_string(int(status)).decode()
+
+
+mg_status_string = status_string
+
+
+def _ptr(t, n: int | None = None, name: str = "vector"):
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda or t.dtype != torch.float64 or not t.is_contiguous():
+        raise TypeError(f"{name} must be a contiguous float64 CUDA tensor")
+    if n is not None and t.numel() != n:
+        raise ValueError(f"{name} has {t.numel()} elements, expected {n}")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    import torch
+    s = torch.cuda.current_stream() if stream is None else stream
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _host(a, n: int, name: str):
+    a = np.ascontiguousarray(np.asarray(a, dtype=np.float64).ravel())
+    if a.size != n:
+        raise ValueError(f"{name} has {a.size} values, expected {n}")
+    return a, a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+@dataclass
+class SolveInfo:
+    status: int
+    iters: int
+    rel_res: float
+    ms: float
+
+    @property
+    def converged(self) -> bool:
+        return self.status == MG_OK
+
+
+class Handle:
+    """An mg_setup handle (owns the multigrid hierarchy and workspace on one GPU)."""
+
+    def __init__(self, ptr: int, n: int, nlev: int, levels: int, ncol: int, ncell: int, nu: int):
+        self._ptr = ctypes.c_void_p(ptr)
+        self.n, self.nlev, self.levels = n, nlev, levels
+        self.ncol, self.ncell, self.nu = ncol, ncell, nu
+
+    def level_cells(self, level: int) -> int:
+        return self.nlev * 6 * (self.n >> level) ** 2
+
+    @property
+    def ptr(self):
+        if not self._ptr:
+            raise ValueError("handle was destroyed")
+        return self._ptr
+
+    def destroy(self):
+        if self._ptr:
+            load().mg_destroy(self._ptr)
+            self._ptr = ctypes.c_void_p(None)
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
+
+
+def _check(st: int, what: str):
+    if st != MG_OK:
+        raise MGError(st, what)
+
+
+def mg_setup(n: int, nlev: int, z_interfaces, g, *, radius: float = 6371.0e3, cs_dt: float = 340.0 * 600.0,
+             levels: int = 4, omega: float = 0.8, n_pre: int = 2, n_post: int = 2, n_coarse: int = 4,
+             precision: str | int = "fp64", gcr_restart: int = 5, max_iter: int = 200,
+             beta_up=None, beta_dn=None, eps: float = 0.0) -> Handle:
+    """Build the hierarchy on the current CUDA device (see mg_setup in mgsolve.h)."""
+    import torch
+    torch.cuda.current_device()   # make sure the device context exists
+    lib = load()
+    ncol = 6 * n * n
+    z, zp = _host(z_interfaces, nlev + 1, "z_interfaces")
+    gg, gp = _host(g, nlev * ncol, "g")
+    mesh = _Mesh(n, nlev, radius, cs_dt, zp)
+    prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+    prm = _Params(levels, omega, n_pre, n_post, n_coarse, prec, gcr_restart, max_iter)
+    mixed = None
+    keep = [z, gg]
+    if beta_up is not None:
+        bu, bup = _host(beta_up, (nlev + 1) * ncol, "beta_up")
+        bd, bdp = _host(beta_dn, (nlev + 1) * ncol, "beta_dn")
+        keep += [bu, bd]
+        mixed = _Mixed(bup, bdp, eps)
+    out = ctypes.c_void_p()
+    st = lib.mg_setup(ctypes.byref(mesh), ctypes.byref(prm), gp,
+                      ctypes.byref(mixed) if mixed is not None else None, ctypes.byref(out))
+    _check(st, "mg_setup")
+    nc, nn, nu = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+    _check(lib.mg_sizes(out, ctypes.byref(nc), ctypes.byref(nn), ctypes.byref(nu)), "mg_sizes")
+    del keep
+    return Handle(out.value, n, nlev, levels, nc.value, nn.value, nu.value)
+
+
+def mg_setup_config(cfg, inp: dict, precision: str | int = "fp64", levels: int | None = None,
+                    mixed: bool | None = None, max_iter: int = 200, **kw) -> Handle:
+    """mg_setup for a synthetic workload (a ``synthetic.Config`` and its input arrays)."""
+    mixed = cfg.mixed if mixed is None else mixed
+    extra = {}
+    if mixed:
+        extra = dict(beta_up=inp["beta_up"], beta_dn=inp["beta_dn"], eps=cfg.eps)
+    return mg_setup(cfg.n, cfg.nlev, inp["z_if"], inp["g"], radius=cfg.radius, cs_dt=cfg.cs * cfg.dt,
+                    levels=levels or cfg.levels, omega=cfg.omega, n_pre=cfg.n_pre, n_post=cfg.n_post,
+                    n_coarse=cfg.n_coarse, precision=precision, gcr_restart=cfg.gcr_restart,
+                    max_iter=max_iter, **extra, **kw)
+
+
+def mg_destroy(h: Handle):
+    h.destroy()
+
+
+def helmholtz_apply(h: Handle, x, y, stream=None):
+    _check(load().helmholtz_apply(h.ptr, _ptr(x, h.ncell, "x"), _ptr(y, h.ncell, "y"), _stream(stream)),
+           "helmholtz_apply")
+
+
+def vcycle(h: Handle, b, x, stream=None):
+    _check(load().vcycle(h.ptr, _ptr(b, h.ncell, "b"), _ptr(x, h.ncell, "x"), _stream(stream)), "vcycle")
+
+
+def _solve_status(st: int, info: _Info, what: str) -> SolveInfo:
+    if st not in (MG_OK, MG_ERR_NOT_CONVERGED, MG_ERR_BREAKDOWN):
+        raise MGError(st, what)
+    return SolveInfo(st, info.iters, info.rel_res, info.ms)
+
+
+def pressure_solve(h: Handle, b, x, tol: float = 1e-8, stream=None) -> SolveInfo:
+    info = _Info()
+    st = load().pressure_solve(h.ptr, _ptr(b, h.ncell, "b"), _ptr(x, h.ncell, "x"), tol, ctypes.byref(info),
+                               _stream(stream))
+    return _solve_status(st, info, "pressure_solve")
+
+
+def mixed_solve(h: Handle, rhs_u, rhs_p, u, p, tol: float = 1e-8, stream=None) -> SolveInfo:
+    info = _Info()
+    st = load().mixed_solve(h.ptr, _ptr(rhs_u, h.nu, "rhs_u"), _ptr(rhs_p, h.ncell, "rhs_p"),
+                            _ptr(u, h.nu, "u"), _ptr(p, h.ncell, "p"), tol, ctypes.byref(info), _stream(stream))
+    return _solve_status(st, info, "mixed_solve")
+
+
+def mg_level_apply(h: Handle, level: int, x, y, stream=None):
+    n = h.level_cells(level)
+    _check(load().mg_level_apply(h.ptr, level, _ptr(x, n, "x"), _ptr(y, n, "y"), _stream(stream)), "mg_level_apply")
+
+
+def mg_smooth(h: Handle, level: int, b, x_in, x_out, sweeps: int, stream=None):
+    n = h.level_cells(level)
+    xin = None if x_in is None else _ptr(x_in, n, "x_in")
+    _check(load().mg_smooth(h.ptr, level, _ptr(b, n, "b"), xin, _ptr(x_out, n, "x_out"), sweeps, _stream(stream)),
+           "mg_smooth")
+
+
+def mg_residual_restrict(h: Handle, level: int, b, x, bc, stream=None):
+    n, nc = h.level_cells(level), h.level_cells(level + 1)
+    _check(load().mg_residual_restrict(h.ptr, level, _ptr(b, n, "b"), _ptr(x, n, "x"), _ptr(bc, nc, "bc"),
+                                       _stream(stream)), "mg_residual_restrict")
+
+
+def mg_prolong_add(h: Handle, level: int, xc, x, stream=None):
+    n, nc = h.level_cells(level), h.level_cells(level + 1)
+    _check(load().mg_prolong_add(h.ptr, level, _ptr(xc, nc, "xc"), _ptr(x, n, "x"), _stream(stream)),
+           "mg_prolong_add")
+
+
+def mixed_apply(h: Handle, u, p, yu, yp, stream=None):
+    _check(load().mixed_apply(h.ptr, _ptr(u, h.nu, "u"), _ptr(p, h.ncell, "p"), _ptr(yu, h.nu, "yu"),
+                              _ptr(yp, h.ncell, "yp"), _stream(stream)), "mixed_apply")
+
+
+def schur_precond(h: Handle, ru, rp, u, p, stream=None):
+    _check(load().schur_precond(h.ptr, _ptr(ru, h.nu, "ru"), _ptr(rp, h.ncell, "rp"), _ptr(u, h.nu, "u"),
+                                _ptr(p, h.ncell, "p"), _stream(stream)), "schur_precond")
+
+
+def mg_profile_start(h: Handle, capacity: int = 65536):
+    """Record every kernel launch of the following calls with CUDA events."""
+    _check(load().mg_profile_start(h.ptr, capacity), "mg_profile_start")
+    h._prof_cap = capacity
+
+
+def mg_profile_stop(h: Handle) -> list[dict]:
+    """Stop recording; returns one dict per timed launch (kind, level, bytes, ms)."""
+    cap = getattr(h, "_prof_cap", 65536)
+    recs = (_KRec * cap)()
+    cnt = ctypes.c_int32()
+    _check(load().mg_profile_stop(h.ptr, recs, cap, ctypes.byref(cnt)), "mg_profile_stop")
+    return [dict(kind=KERNEL_KINDS[r.kind], level=r.level, bytes=r.bytes, ms=r.ms) for r in recs[:min(cnt.value, cap)]]

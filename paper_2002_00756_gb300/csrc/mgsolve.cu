@@ -1,0 +1,836 @@
+// C ABI of the GB300 column multigrid solver: handle, set-up, V-cycle driver (Algorithm 1),
+// GCR outer solves and the mixed-system Schur-complement preconditioner.
+// See include/mgsolve.h for the contract of every entry point.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/mgsolve.h"
+#include "kernels.cuh"
+#include "krylov.cuh"
+#include "mesh.h"
+
+using mg::Lvl;
+typedef __nv_bfloat16 bf16;
+
+namespace {
+
+struct DevLevel {
+    int n = 0, ncol = 0;
+    int32_t* nbr = nullptr;
+    int32_t* fof = nullptr;
+    double* rA64 = nullptr;
+    float* rA32 = nullptr;
+    double* Th64 = nullptr;
+    double* Tv64 = nullptr;
+    float* Th32 = nullptr;
+    float* Tv32 = nullptr;
+    bf16* Th16 = nullptr;
+    bf16* Tv16 = nullptr;
+    double* w64 = nullptr;  // restriction weights onto the next level, [4][ncol_next]
+    float* w32 = nullptr;
+    // workspace: two iterates, the level's rhs and the result handed to the finer level
+    double* x64[2] = {nullptr, nullptr};
+    double* b64 = nullptr;
+    double* r64 = nullptr;
+    float* x32[2] = {nullptr, nullptr};
+    float* b32 = nullptr;
+    float* r32 = nullptr;
+};
+
+}  // namespace
+
+struct mg_handle {
+    int device = 0;
+    int L = 0, nlev = 0, n = 0;
+    int nsm = 0;
+    mg_params prm{};
+    std::vector<DevLevel> lv;
+    double* rdz64 = nullptr;
+    float* rdz32 = nullptr;
+    // GCR
+    size_t glen = 0;            // length of a GCR vector (N, or nu + N with mixed data)
+    double* Z = nullptr;        // [restart][glen]
+    double* W = nullptr;        // [restart][glen]
+    double* r = nullptr;        // [glen]
+    double* sc = nullptr;       // device scalars
+    double* partials = nullptr;
+    unsigned int* tickets = nullptr;
+    double* host_sc = nullptr;  // pinned
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    int red_grid = 0;
+    // mixed
+    bool mixed = false;
+    int64_t nu = 0;
+    mg::MixedDev md{};
+    double* schurB = nullptr;
+    double* mb = nullptr;       // concatenated mixed rhs [nu + N]
+    double* mx = nullptr;       // concatenated mixed solution [nu + N]
+    std::vector<void*> allocs;
+    // per-launch event profiling (mg_profile_start / mg_profile_stop)
+    struct Rec {
+        int kind, level;
+        double bytes;
+    };
+    bool prof = false;
+    std::vector<cudaEvent_t> evpool;
+    std::vector<Rec> recs;
+};
+
+namespace {
+
+// device scalar slots
+enum { SC_DOTS = 0, SC_WW = SC_DOTS + mg::MAXR, SC_ALPHA = SC_WW + mg::MAXR, SC_RR, SC_BB, SC_TMP, SC_COUNT = SC_TMP + 4 };
+enum { TK_DOT = 0, TK_DOTS, TK_ORTH, TK_UPD, TK_COUNT };
+
+#define CK(call)                                   \
+    do {                                           \
+        cudaError_t e_ = (call);                   \
+        if (e_ != cudaSuccess) return MG_ERR_CUDA; \
+    } while (0)
+
+template <typename P>
+mg_status dalloc(mg_handle* h, P** p, size_t count) {
+    *p = nullptr;
+    if (count == 0) return MG_OK;
+    void* q = nullptr;
+    if (cudaMalloc(&q, count * sizeof(P)) != cudaSuccess) {
+        cudaGetLastError();
+        return MG_ERR_NOMEM;
+    }
+    h->allocs.push_back(q);
+    *p = static_cast<P*>(q);
+    return MG_OK;
+}
+
+template <typename P, typename S>
+mg_status upload(mg_handle* h, P** p, const std::vector<S>& src) {
+    mg_status st = dalloc(h, p, src.size());
+    if (st != MG_OK) return st;
+    if (src.empty()) return MG_OK;
+    std::vector<P> tmp(src.size());
+    for (size_t i = 0; i < src.size(); ++i) tmp[i] = (P)src[i];
+    CK(cudaMemcpy(*p, tmp.data(), tmp.size() * sizeof(P), cudaMemcpyHostToDevice));
+    return MG_OK;
+}
+
+template <>
+mg_status upload<bf16, double>(mg_handle* h, bf16** p, const std::vector<double>& src) {
+    mg_status st = dalloc(h, p, src.size());
+    if (st != MG_OK) return st;
+    std::vector<bf16> tmp(src.size());
+    for (size_t i = 0; i < src.size(); ++i) tmp[i] = __float2bfloat16_rn((float)src[i]);
+    CK(cudaMemcpy(*p, tmp.data(), tmp.size() * sizeof(bf16), cudaMemcpyHostToDevice));
+    return MG_OK;
+}
+
+#define TRY(call)                         \
+    do {                                  \
+        mg_status s_ = (call);            \
+        if (s_ != MG_OK) return s_;       \
+    } while (0)
+
+inline cudaStream_t S(void* s) { return static_cast<cudaStream_t>(s); }
+
+inline size_t cells(const mg_handle* h, int l) { return (size_t)h->nlev * h->lv[l].ncol; }
+
+// Brackets one kernel launch with a pair of events when profiling is on.  `bytes` is the
+// algorithmic traffic of the launch: every array element the kernel must read or write,
+// counted once (neighbour re-reads within a launch are cache traffic, not counted).
+struct Prof {
+    mg_handle* h;
+    cudaStream_t s;
+    int idx = -1;
+    Prof(mg_handle* h_, int kind, int level, double bytes, cudaStream_t s_) : h(h_), s(s_) {
+        if (h && h->prof && 2 * (h->recs.size() + 1) <= h->evpool.size()) {
+            idx = (int)h->recs.size();
+            h->recs.push_back({kind, level, bytes});
+            cudaEventRecord(h->evpool[2 * idx], s);
+        }
+    }
+    ~Prof() {
+        if (idx >= 0) cudaEventRecord(h->evpool[2 * idx + 1], s);
+    }
+};
+
+// ---- per-precision views of a level ----
+template <typename T, typename C>
+struct View;
+
+template <>
+struct View<double, double> {
+    static Lvl<double, double> lvl(const mg_handle* h, int l) {
+        const DevLevel& d = h->lv[l];
+        return {d.n, d.ncol, h->nlev, d.nbr, d.fof, d.Th64, d.Tv64, d.rA64, h->rdz64};
+    }
+    static double* x(DevLevel& d, int i) { return d.x64[i]; }
+    static double* b(DevLevel& d) { return d.b64; }
+    static double* r(DevLevel& d) { return d.r64; }
+    static const double* w(const DevLevel& d) { return d.w64; }
+};
+template <>
+struct View<float, float> {
+    static Lvl<float, float> lvl(const mg_handle* h, int l) {
+        const DevLevel& d = h->lv[l];
+        return {d.n, d.ncol, h->nlev, d.nbr, d.fof, d.Th32, d.Tv32, d.rA32, h->rdz32};
+    }
+    static float* x(DevLevel& d, int i) { return d.x32[i]; }
+    static float* b(DevLevel& d) { return d.b32; }
+    static float* r(DevLevel& d) { return d.r32; }
+    static const float* w(const DevLevel& d) { return d.w32; }
+};
+template <>
+struct View<float, bf16> {
+    static Lvl<float, bf16> lvl(const mg_handle* h, int l) {
+        const DevLevel& d = h->lv[l];
+        return {d.n, d.ncol, h->nlev, d.nbr, d.fof, d.Th16, d.Tv16, d.rA32, h->rdz32};
+    }
+    static float* x(DevLevel& d, int i) { return d.x32[i]; }
+    static float* b(DevLevel& d) { return d.b32; }
+    static float* r(DevLevel& d) { return d.r32; }
+    static const float* w(const DevLevel& d) { return d.w32; }
+};
+
+constexpr size_t SWEEP_SMEM_MAX = 200 * 1024;
+
+inline int sweep_block(int ncol) {
+    if (ncol >= 128 * 300) return 128;
+    if (ncol >= 64 * 300) return 64;
+    return 32;
+}
+
+// ---- launchers ----
+template <typename T, typename C, typename X, typename Y>
+mg_status launch_apply(mg_handle* h, int lev, const Lvl<T, C>& L, const X* x, Y* y, cudaStream_t s) {
+    const double nc = (double)L.nlev * L.ncol;
+    Prof pr(h, MG_K_APPLY, lev, nc * (sizeof(X) + 3 * sizeof(C) + sizeof(Y)), s);
+    const int bd = 128;
+    const long target = 4L * 152 * 256;
+    int kc = (int)((long)L.nlev * L.ncol / target);
+    kc = kc < 4 ? 4 : (kc > L.nlev ? L.nlev : kc);
+    dim3 grid((L.ncol + bd - 1) / bd, (L.nlev + kc - 1) / kc);
+    mg::k_apply<T, C, X, Y><<<grid, bd, 0, s>>>(L, x, y, kc);
+    CK(cudaGetLastError());
+    return MG_OK;
+}
+
+template <typename T, typename C, int MODE, typename X, typename B, typename O, bool BCOPY>
+mg_status launch_sweep(mg_handle* h, int lev, const Lvl<T, C>& L, const X* x, const T* xc, int ncol_c,
+                       const B* b, T* bcopy, O* xo, double omega, cudaStream_t s) {
+    const double nc = (double)L.nlev * L.ncol;
+    double per = sizeof(B) + 3 * sizeof(C) + sizeof(O);
+    if (MODE == mg::XM_PLAIN || MODE == mg::XM_PROLONG) per += sizeof(X);
+    if (MODE == mg::XM_PROLONG || MODE == mg::XM_PROLONG0) per += 0.25 * sizeof(T);
+    if (BCOPY) per += sizeof(T);
+    Prof pr(h, MG_K_SWEEP, lev, nc * per, s);
+    // the column stash (2 values per level per thread) must fit the shared-memory budget
+    int bd = sweep_block(L.ncol);
+    const int cap = (int)(SWEEP_SMEM_MAX / (2 * (size_t)L.nlev * sizeof(T))) / 32 * 32;
+    if (cap < 32) return MG_ERR_UNSUPPORTED;
+    if (bd > cap) bd = cap;
+    const size_t smem = 2 * (size_t)L.nlev * bd * sizeof(T);
+    if (smem > 48 * 1024)
+        CK(cudaFuncSetAttribute(mg::k_sweep<T, C, MODE, X, B, O, BCOPY>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    const int grid = (L.ncol + bd - 1) / bd;
+    mg::k_sweep<T, C, MODE, X, B, O, BCOPY><<<grid, bd, smem, s>>>(L, x, xc, ncol_c, b, bcopy, xo, (T)omega);
+    CK(cudaGetLastError());
+    return MG_OK;
+}
+
+template <typename T, typename C, bool XZERO, typename X, typename B, typename O>
+mg_status launch_restrict(mg_handle* h, int lev, const Lvl<T, C>& L, const X* x, const B* b, const T* w, O* bc,
+                          int ncol_c, cudaStream_t s) {
+    const double nc = (double)L.nlev * L.ncol;
+    Prof pr(h, MG_K_RESTRICT, lev, nc * (sizeof(B) + 3 * sizeof(C) + (XZERO ? 0 : sizeof(X)) + 0.25 * sizeof(O) +
+                                          sizeof(T) / (double)L.nlev), s);
+    const int bd = ncol_c >= 128 * 300 ? 128 : (ncol_c >= 64 * 300 ? 64 : 32);
+    mg::k_resid_restrict<T, C, XZERO, X, B, O><<<(ncol_c + bd - 1) / bd, bd, 0, s>>>(L, x, b, w, bc, ncol_c);
+    CK(cudaGetLastError());
+    return MG_OK;
+}
+
+template <typename T, bool ZB, typename X, typename O>
+mg_status launch_prolong(mg_handle* h, int lev, int n, int ncol, int ncol_c, int nlev, const X* x, const T* xc,
+                         O* xo, cudaStream_t s) {
+    Prof pr(h, MG_K_PROLONG, lev, (double)nlev * ncol * (0.25 * sizeof(T) + (ZB ? 0 : sizeof(X)) + sizeof(O)), s);
+    const int bd = 128;
+    mg::k_prolong<T, ZB, X, O><<<(ncol + bd - 1) / bd, bd, 0, s>>>(n, ncol, ncol_c, nlev, x, xc, xo);
+    CK(cudaGetLastError());
+    return MG_OK;
+}
+
+template <typename A, typename B>
+mg_status launch_convert(mg_handle* h, int lev, size_t n, const A* a, B* b, cudaStream_t s) {
+    Prof pr(h, MG_K_CONVERT, lev, (double)n * (sizeof(A) + sizeof(B)), s);
+    mg::k_convert<A, B><<<4 * 152, 256, 0, s>>>(n, a, b);
+    CK(cudaGetLastError());
+    return MG_OK;
+}
+
+// One sweep with the iterate source chosen at run time.
+//   cur == nullptr and xc == nullptr : zero iterate
+//   xc != nullptr                    : iterate = (cur or 0) + Prolongate(xc)
+template <typename T, typename C, typename B, typename O>
+mg_status sweep_any(mg_handle* h, int lev, const Lvl<T, C>& L, const T* cur, const T* xc, int ncol_c, const B* b,
+                    T* bcopy, O* xo, double om, cudaStream_t s) {
+    if (bcopy) {
+        if (xc) return MG_ERR_ARG;
+        if (cur) return launch_sweep<T, C, mg::XM_PLAIN, T, B, O, true>(h, lev, L, cur, xc, ncol_c, b, bcopy, xo, om, s);
+        return launch_sweep<T, C, mg::XM_ZERO, T, B, O, true>(h, lev, L, cur, xc, ncol_c, b, bcopy, xo, om, s);
+    }
+    if (xc) {
+        if (cur)
+            return launch_sweep<T, C, mg::XM_PROLONG, T, B, O, false>(h, lev, L, cur, xc, ncol_c, b, bcopy, xo, om, s);
+        return launch_sweep<T, C, mg::XM_PROLONG0, T, B, O, false>(h, lev, L, cur, xc, ncol_c, b, bcopy, xo, om, s);
+    }
+    if (cur) return launch_sweep<T, C, mg::XM_PLAIN, T, B, O, false>(h, lev, L, cur, xc, ncol_c, b, bcopy, xo, om, s);
+    return launch_sweep<T, C, mg::XM_ZERO, T, B, O, false>(h, lev, L, cur, xc, ncol_c, b, bcopy, xo, om, s);
+}
+
+// Algorithm 1 on level l with right-hand side `b` (type B: FP64 on the finest level of the
+// FP32 V-cycle, T otherwise); the result goes to `out` (type O).  On every level the
+// iterate starts at zero (x^(l+1) <- 0 of Algorithm 1; the V-cycle is used as a
+// preconditioner, so x^(1) = 0 as well).
+template <typename T, typename C, typename B, typename O>
+mg_status mgv(mg_handle* h, int l, const B* b, O* out, cudaStream_t s) {
+    typedef View<T, C> V;
+    DevLevel& d = h->lv[l];
+    const Lvl<T, C> L = V::lvl(h, l);
+    const bool coarsest = (l == h->L - 1);
+    const double om = h->prm.omega;
+    const bool conv = !std::is_same<B, T>::value;  // rhs arrives in FP64, iterate in FP32
+    T* ws[2] = {V::x(d, 0), V::x(d, 1)};
+    const T* bT = conv ? (const T*)V::b(d) : (const T*)(const void*)b;
+    const int npre = coarsest ? h->prm.n_coarse : h->prm.n_pre;
+    if (conv && npre == 0) TRY(launch_convert(h, l, cells(h, l), b, V::b(d), s));
+    T* cur = nullptr;
+    for (int i = 0; i < npre; ++i) {
+        const bool final = coarsest && i == npre - 1;
+        T* dst = (cur == ws[0]) ? ws[1] : ws[0];
+        T* bcopy = (conv && i == 0) ? V::b(d) : nullptr;
+        if (final) {
+            if (i == 0) TRY((sweep_any<T, C, B, O>(h, l, L, cur, (const T*)nullptr, 0, b, bcopy, out, om, s)));
+            else TRY((sweep_any<T, C, T, O>(h, l, L, cur, (const T*)nullptr, 0, bT, nullptr, out, om, s)));
+            return MG_OK;
+        }
+        if (i == 0) TRY((sweep_any<T, C, B, T>(h, l, L, cur, (const T*)nullptr, 0, b, bcopy, dst, om, s)));
+        else TRY((sweep_any<T, C, T, T>(h, l, L, cur, (const T*)nullptr, 0, bT, nullptr, dst, om, s)));
+        cur = dst;
+    }
+    // residual and restriction onto level l+1
+    DevLevel& dc = h->lv[l + 1];
+    T* bc = V::b(dc);
+    if (cur) TRY((launch_restrict<T, C, false, T, T, T>(h, l, L, cur, bT, V::w(d), bc, dc.ncol, s)));
+    else TRY((launch_restrict<T, C, true, T, T, T>(h, l, L, cur, bT, V::w(d), bc, dc.ncol, s)));
+    T* xc = V::r(dc);
+    TRY((mgv<T, C, T, T>(h, l + 1, bc, xc, s)));
+    // coarse-grid correction fused into the first post-smoothing sweep
+    const int npost = h->prm.n_post;
+    if (npost == 0) {
+        if (cur) return launch_prolong<T, false, T, O>(h, l, d.n, d.ncol, dc.ncol, h->nlev, cur, xc, out, s);
+        return launch_prolong<T, true, T, O>(h, l, d.n, d.ncol, dc.ncol, h->nlev, cur, xc, out, s);
+    }
+    for (int i = 0; i < npost; ++i) {
+        const T* pxc = (i == 0) ? xc : nullptr;
+        const int ncc = (i == 0) ? dc.ncol : 0;
+        if (i == npost - 1) return sweep_any<T, C, T, O>(h, l, L, cur, pxc, ncc, bT, nullptr, out, om, s);
+        T* dst = (cur == ws[0]) ? ws[1] : ws[0];
+        TRY((sweep_any<T, C, T, T>(h, l, L, cur, pxc, ncc, bT, nullptr, dst, om, s)));
+        cur = dst;
+    }
+    return MG_OK;
+}
+
+mg_status run_vcycle(mg_handle* h, const double* b, double* x, cudaStream_t s) {
+    switch (h->prm.vcycle_precision) {
+        case MG_FP64: return mgv<double, double, double, double>(h, 0, b, x, s);
+        case MG_FP32: return mgv<float, float, double, double>(h, 0, b, x, s);
+        case MG_FP32_BF16COEF: return mgv<float, bf16, double, double>(h, 0, b, x, s);
+        default: return MG_ERR_ARG;
+    }
+}
+
+// ---- GCR (Sec. 4.1; textbook generalised conjugate residual, right preconditioned) ----
+template <typename ApplyA, typename ApplyP>
+mg_status gcr(mg_handle* h, size_t n, const double* b, double* x, double tol, mg_solve_info* info,
+              cudaStream_t s, ApplyA applyA, ApplyP applyP) {
+    const int m = h->prm.gcr_restart;
+    const int G = h->red_grid;
+    double* sc = h->sc;
+    CK(cudaEventRecord(h->ev0, s));
+    CK(cudaMemcpyAsync(h->r, b, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    CK(cudaMemsetAsync(x, 0, n * sizeof(double), s));
+    {
+        Prof pr(h, MG_K_DOT, 0, 8.0 * n, s);
+        mg::k_dot<<<G, mg::RED_THREADS, 0, s>>>(n, b, b, h->partials, h->tickets + TK_DOT, sc + SC_BB);
+        CK(cudaGetLastError());
+    }
+    CK(cudaMemcpyAsync(h->host_sc, sc + SC_BB, sizeof(double), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    const double bb = h->host_sc[0];
+    mg_status st = MG_OK;
+    int it = 0;
+    double rel = 0.0;
+    if (!std::isfinite(bb)) st = MG_ERR_BREAKDOWN;
+    else if (bb > 0.0) {
+        rel = 1.0;
+        st = MG_ERR_NOT_CONVERGED;
+        for (it = 0; it < h->prm.max_iter;) {
+            const int j = it % m;
+            double* z = h->Z + (size_t)j * h->glen;
+            double* w = h->W + (size_t)j * h->glen;
+            TRY(applyP(h->r, z));
+            TRY(applyA(z, w));
+            if (j > 0) {
+                Prof pr(h, MG_K_GCR_DOTS, 0, 8.0 * n * (j + 1), s);
+                mg::k_gcr_dots<<<G, mg::RED_THREADS, 0, s>>>(n, w, h->W, h->glen, j, h->partials,
+                                                              h->tickets + TK_DOTS, sc + SC_DOTS);
+                CK(cudaGetLastError());
+            }
+            {
+                Prof pr(h, MG_K_GCR_ORTH, 0, 8.0 * n * (j > 0 ? 2 * j + 5 : 2), s);
+                mg::k_gcr_orth<<<G, mg::RED_THREADS, 0, s>>>(n, w, z, h->W, h->Z, h->glen, j, sc + SC_DOTS, sc + SC_WW,
+                                                          h->r, h->partials, h->tickets + TK_ORTH, sc + SC_TMP,
+                                                          sc + SC_ALPHA);
+                CK(cudaGetLastError());
+            }
+            {
+                Prof pr(h, MG_K_GCR_UPDATE, 0, 8.0 * n * 6, s);
+                mg::k_gcr_update<<<G, mg::RED_THREADS, 0, s>>>(n, x, h->r, z, w, sc + SC_ALPHA, h->partials,
+                                                            h->tickets + TK_UPD, sc + SC_RR);
+                CK(cudaGetLastError());
+            }
+            CK(cudaMemcpyAsync(h->host_sc, sc + SC_RR, sizeof(double), cudaMemcpyDeviceToHost, s));
+            CK(cudaStreamSynchronize(s));
+            ++it;
+            const double rr = h->host_sc[0];
+            if (!std::isfinite(rr)) {
+                st = MG_ERR_BREAKDOWN;
+                break;
+            }
+            rel = std::sqrt(rr / bb);
+            if (rel <= tol) {
+                st = MG_OK;
+                break;
+            }
+        }
+    }
+    CK(cudaEventRecord(h->ev1, s));
+    CK(cudaEventSynchronize(h->ev1));
+    if (info) {
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, h->ev0, h->ev1);
+        info->iters = it;
+        info->rel_res = rel;
+        info->ms = ms;
+    }
+    return st;
+}
+
+// ---- mixed operator and Schur-complement preconditioner ----
+mg_status mixed_apply_impl(mg_handle* h, const double* u, const double* p, double* yu, double* yp, cudaStream_t s) {
+    const mg::MixedDev& M = h->md;
+    const size_t nh = (size_t)M.nlev * M.nfh;
+    const int bd = 128;
+    Prof pr(h, MG_K_MIXED, 0, 8.0 * (2.0 * h->nu + 3.0 * cells(h, 0)), s);
+    mg::k_mx_faces_h<0><<<dim3((M.nfh + bd - 1) / bd, M.nlev), bd, 0, s>>>(M, u, p, yu);
+    mg::k_mx_faces_v<0><<<dim3((M.ncol + bd - 1) / bd, M.nlev + 1), bd, 0, s>>>(M, u + nh, p, yu + nh);
+    mg::k_mx_cells<0><<<dim3((M.ncol + bd - 1) / bd, M.nlev), bd, 0, s>>>(M, u, u + nh, p, yp);
+    CK(cudaGetLastError());
+    return MG_OK;
+}
+
+mg_status schur_impl(mg_handle* h, const double* ru, const double* rp, double* u, double* p, cudaStream_t s) {
+    const mg::MixedDev& M = h->md;
+    const size_t nh = (size_t)M.nlev * M.nfh;
+    const int bd = 128;
+    // Step 1: B = r_p - D M-ring^{-1} r_u
+    mg::k_mx_cells<1><<<dim3((M.ncol + bd - 1) / bd, M.nlev), bd, 0, s>>>(M, ru, ru + nh, rp, h->schurB);
+    CK(cudaGetLastError());
+    // Step 2: one V-cycle for H Pi' = B
+    TRY(run_vcycle(h, h->schurB, p, s));
+    // Step 3: u' = M-ring^{-1} (r_u - G Pi')
+    mg::k_mx_faces_h<1><<<dim3((M.nfh + bd - 1) / bd, M.nlev), bd, 0, s>>>(M, ru, p, u);
+    mg::k_mx_faces_v<1><<<dim3((M.ncol + bd - 1) / bd, M.nlev + 1), bd, 0, s>>>(M, ru + nh, p, u + nh);
+    CK(cudaGetLastError());
+    return MG_OK;
+}
+
+mg_status check_level(const mg_handle* h, int level) {
+    if (!h || level < 0 || level >= h->L) return MG_ERR_ARG;
+    return MG_OK;
+}
+
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) == cudaSuccess && prev != dev) cudaSetDevice(dev);
+        else prev = -1;
+    }
+    ~DeviceGuard() {
+        if (prev >= 0) cudaSetDevice(prev);
+    }
+};
+
+mg_status setup_impl(mg_handle* h, const mg_mesh* mesh, const mg_params* prm, const double* g,
+                     const mg_mixed* mixed) {
+    const int L = prm->levels, n = mesh->n, nlev = mesh->nlev;
+    h->L = L;
+    h->n = n;
+    h->nlev = nlev;
+    h->prm = *prm;
+    CK(cudaGetDevice(&h->device));
+    CK(cudaDeviceGetAttribute(&h->nsm, cudaDevAttrMultiProcessorCount, h->device));
+    h->red_grid = 2 * h->nsm;
+    // host hierarchy
+    std::vector<mg::HGeom> hg(L);
+    for (int l = 0; l < L; ++l) {
+        const std::string err = mg::build_hgeom(n >> l, mesh->radius, hg[l]);
+        if (!err.empty()) return MG_ERR_ARG;
+    }
+    mg::VGeom vg;
+    if (!mg::build_vgeom(mesh->z_interfaces, nlev, vg).empty()) return MG_ERR_ARG;
+    const int ncol0 = hg[0].ncol;
+    const size_t N0 = (size_t)nlev * ncol0, NV0 = (size_t)(nlev + 1) * ncol0;
+    std::vector<mg::LevelCoef> co(L);
+    co[0].g.assign(g, g + N0);
+    for (size_t i = 0; i < N0; ++i)
+        if (!(g[i] > 0.0) || !std::isfinite(g[i])) return MG_ERR_ARG;
+    co[0].mu.assign(NV0, 1.0);
+    std::vector<double> w_up, w_dn, mlump;
+    if (mixed) {
+        w_up.assign(NV0, 0.0);
+        w_dn.assign(NV0, 0.0);
+        mlump.assign(NV0, 1.0);
+        for (int kf = 1; kf < nlev; ++kf) {
+            for (int c = 0; c < ncol0; ++c) {
+                const size_t o = (size_t)kf * ncol0 + c;
+                if (kf + 1 <= nlev - 1) w_up[o] = mixed->eps * mixed->beta_up[o];
+                if (kf - 1 >= 1) w_dn[o] = mixed->eps * mixed->beta_dn[o];
+                mlump[o] = 1.0 + w_up[o] + w_dn[o];
+                co[0].mu[o] = 1.0 / mlump[o];
+            }
+        }
+    }
+    for (int l = 1; l < L; ++l) {
+        co[l].g.resize((size_t)nlev * hg[l].ncol);
+        co[l].mu.resize((size_t)(nlev + 1) * hg[l].ncol);
+        mg::restrict_mean(hg[l - 1], hg[l], nlev, co[l - 1].g.data(), co[l].g.data());
+        mg::restrict_mean(hg[l - 1], hg[l], nlev + 1, co[l - 1].mu.data(), co[l].mu.data());
+    }
+    for (int l = 0; l < L; ++l) mg::level_coefficients(hg[l], vg, mesh->cs_dt, co[l]);
+    // upload
+    std::vector<double> rdz(nlev);
+    for (int k = 0; k < nlev; ++k) rdz[k] = 1.0 / vg.dz[k];
+    TRY(upload(h, &h->rdz64, rdz));
+    TRY(upload(h, &h->rdz32, rdz));
+    const int prec = prm->vcycle_precision;
+    h->lv.resize(L);
+    for (int l = 0; l < L; ++l) {
+        DevLevel& d = h->lv[l];
+        const mg::HGeom& G = hg[l];
+        d.n = G.n;
+        d.ncol = G.ncol;
+        std::vector<double> rA(G.ncol);
+        for (int c = 0; c < G.ncol; ++c) rA[c] = 1.0 / G.area[c];
+        TRY(upload(h, &d.nbr, G.nbr));
+        TRY(upload(h, &d.fof, G.face_of));
+        TRY(upload(h, &d.rA64, rA));
+        TRY(upload(h, &d.Th64, co[l].Th));
+        TRY(upload(h, &d.Tv64, co[l].Tv));
+        const size_t Nl = (size_t)nlev * G.ncol;
+        TRY(dalloc(h, &d.x64[0], Nl));
+        TRY(dalloc(h, &d.x64[1], Nl));
+        TRY(dalloc(h, &d.b64, Nl));
+        TRY(dalloc(h, &d.r64, Nl));
+        if (prec != MG_FP64) {
+            TRY(upload(h, &d.rA32, rA));
+            if (prec == MG_FP32) {
+                TRY(upload(h, &d.Th32, co[l].Th));
+                TRY(upload(h, &d.Tv32, co[l].Tv));
+            } else {
+                TRY(upload(h, &d.Th16, co[l].Th));
+                TRY(upload(h, &d.Tv16, co[l].Tv));
+            }
+            TRY(dalloc(h, &d.x32[0], Nl));
+            TRY(dalloc(h, &d.x32[1], Nl));
+            TRY(dalloc(h, &d.b32, Nl));
+            TRY(dalloc(h, &d.r32, Nl));
+        }
+        if (l + 1 < L) {
+            const mg::HGeom& Gc = hg[l + 1];
+            std::vector<double> w(4 * (size_t)Gc.ncol);
+            for (int C = 0; C < Gc.ncol; ++C)
+                for (int q = 0; q < 4; ++q) w[(size_t)q * Gc.ncol + C] = G.area[mg::child_col(G.n, C, q)] / Gc.area[C];
+            TRY(upload(h, &d.w64, w));
+            if (prec != MG_FP64) TRY(upload(h, &d.w32, w));
+        }
+    }
+    // mixed system arrays (finest level)
+    h->mixed = mixed != nullptr;
+    if (h->mixed) {
+        const mg::HGeom& G = hg[0];
+        const int nfh = 2 * ncol0;
+        const double c2 = mesh->cs_dt * mesh->cs_dt;
+        std::vector<double> kd_h((size_t)nlev * nfh), kd_v(NV0, 0.0), sdiv(4 * (size_t)ncol0);
+        for (int f = 0; f < nfh; ++f) {
+            const int Lc = G.faceL[f], Rc = G.faceR[f], sd = G.faceSide[f];
+            const double dist = G.cdist[sd * ncol0 + Lc];
+            for (int k = 0; k < nlev; ++k)
+                kd_h[(size_t)k * nfh + f] = c2 * 0.5 * (g[(size_t)k * ncol0 + Lc] + g[(size_t)k * ncol0 + Rc]) / dist;
+        }
+        for (int kf = 1; kf < nlev; ++kf)
+            for (int c = 0; c < ncol0; ++c)
+                kd_v[(size_t)kf * ncol0 + c] = c2 * 0.5 * (g[(size_t)(kf - 1) * ncol0 + c] + g[(size_t)kf * ncol0 + c]) / vg.dzc[kf];
+        for (int c = 0; c < ncol0; ++c)
+            for (int sd = 0; sd < 4; ++sd) {
+                const int f = G.face_of[sd * ncol0 + c];
+                const double sgn = (G.faceL[f] == c) ? 1.0 : -1.0;
+                sdiv[(size_t)sd * ncol0 + c] = sgn * G.edge_len[sd * ncol0 + c] / G.area[c];
+            }
+        int32_t *fL, *fR;
+        double *dkd_h, *dkd_v, *dsdiv, *dwu, *dwd, *dml;
+        TRY(upload(h, &fL, G.faceL));
+        TRY(upload(h, &fR, G.faceR));
+        TRY(upload(h, &dkd_h, kd_h));
+        TRY(upload(h, &dkd_v, kd_v));
+        TRY(upload(h, &dsdiv, sdiv));
+        TRY(upload(h, &dwu, w_up));
+        TRY(upload(h, &dwd, w_dn));
+        TRY(upload(h, &dml, mlump));
+        h->md = mg::MixedDev{ncol0, nlev, nfh, fL, fR, h->lv[0].fof, dsdiv, dkd_h, dkd_v, dwu, dwd, dml, h->rdz64};
+        h->nu = (int64_t)nlev * nfh + (int64_t)NV0;
+        TRY(dalloc(h, &h->schurB, N0));
+        TRY(dalloc(h, &h->mb, (size_t)h->nu + N0));
+        TRY(dalloc(h, &h->mx, (size_t)h->nu + N0));
+    }
+    // GCR workspace
+    h->glen = N0 + (size_t)h->nu;
+    TRY(dalloc(h, &h->Z, (size_t)prm->gcr_restart * h->glen));
+    TRY(dalloc(h, &h->W, (size_t)prm->gcr_restart * h->glen));
+    TRY(dalloc(h, &h->r, h->glen));
+    TRY(dalloc(h, &h->sc, SC_COUNT));
+    TRY(dalloc(h, &h->partials, (size_t)h->red_grid * mg::MAXR));
+    TRY(dalloc(h, &h->tickets, TK_COUNT));
+    CK(cudaMemset(h->tickets, 0, TK_COUNT * sizeof(unsigned int)));
+    CK(cudaMemset(h->sc, 0, SC_COUNT * sizeof(double)));
+    if (cudaMallocHost(&h->host_sc, 4 * sizeof(double)) != cudaSuccess) return MG_ERR_NOMEM;
+    CK(cudaEventCreate(&h->ev0));
+    CK(cudaEventCreate(&h->ev1));
+    CK(cudaDeviceSynchronize());
+    return MG_OK;
+}
+
+void free_handle(mg_handle* h) {
+    if (!h) return;
+    for (void* p : h->allocs) cudaFree(p);
+    if (h->host_sc) cudaFreeHost(h->host_sc);
+    if (h->ev0) cudaEventDestroy(h->ev0);
+    if (h->ev1) cudaEventDestroy(h->ev1);
+    for (cudaEvent_t e : h->evpool) cudaEventDestroy(e);
+    delete h;
+}
+
+}  // namespace
+
+// =====================================================================================
+extern "C" {
+
+const char* mg_status_string(mg_status s) {
+    switch (s) {
+        case MG_OK: return "ok";
+        case MG_ERR_ARG: return "invalid argument";
+        case MG_ERR_CUDA: return "CUDA runtime error";
+        case MG_ERR_NOMEM: return "out of memory";
+        case MG_ERR_NOT_CONVERGED: return "not converged within max_iter";
+        case MG_ERR_BREAKDOWN: return "Krylov breakdown (zero or non-finite scalar)";
+        case MG_ERR_TIMEOUT: return "device wait timed out";
+        case MG_ERR_UNSUPPORTED: return "unsupported request for this handle";
+    }
+    return "unknown status";
+}
+
+mg_status mg_setup(const mg_mesh* mesh, const mg_params* prm, const double* g, const mg_mixed* mixed,
+                   mg_handle** out) {
+    if (!out) return MG_ERR_ARG;
+    *out = nullptr;
+    if (!mesh || !prm || !g || !mesh->z_interfaces) return MG_ERR_ARG;
+    if (mesh->n < 1 || mesh->nlev < 1 || mesh->nlev > MG_MAX_NLEV) return MG_ERR_ARG;
+    if (!(mesh->radius > 0.0) || !(mesh->cs_dt > 0.0) || !std::isfinite(mesh->cs_dt)) return MG_ERR_ARG;
+    if (prm->levels < 1 || prm->levels > MG_MAX_LEVELS) return MG_ERR_ARG;
+    if (mesh->n % (1 << (prm->levels - 1)) != 0) return MG_ERR_ARG;
+    if (!std::isfinite(prm->omega) || prm->n_pre < 0 || prm->n_post < 0 || prm->n_coarse < 1) return MG_ERR_ARG;
+    if (prm->vcycle_precision < MG_FP64 || prm->vcycle_precision > MG_FP32_BF16COEF) return MG_ERR_ARG;
+    if (prm->gcr_restart < 1 || prm->gcr_restart > MG_MAX_RESTART || prm->max_iter < 1) return MG_ERR_ARG;
+    if (mixed && (!mixed->beta_up || !mixed->beta_dn || !std::isfinite(mixed->eps) || mixed->eps < 0.0))
+        return MG_ERR_ARG;
+    mg_handle* h = new (std::nothrow) mg_handle();
+    if (!h) return MG_ERR_NOMEM;
+    mg_status st = setup_impl(h, mesh, prm, g, mixed);
+    if (st != MG_OK) {
+        free_handle(h);
+        return st;
+    }
+    *out = h;
+    return MG_OK;
+}
+
+void mg_destroy(mg_handle* h) {
+    if (!h) return;
+    DeviceGuard dg(h->device);
+    cudaDeviceSynchronize();
+    free_handle(h);
+}
+
+mg_status mg_sizes(const mg_handle* h, int64_t* ncol, int64_t* ncell, int64_t* nu) {
+    if (!h) return MG_ERR_ARG;
+    if (ncol) *ncol = h->lv[0].ncol;
+    if (ncell) *ncell = (int64_t)cells(h, 0);
+    if (nu) *nu = h->nu;
+    return MG_OK;
+}
+
+mg_status helmholtz_apply(mg_handle* h, const double* x, double* y, void* stream) {
+    if (!h || !x || !y || x == y) return MG_ERR_ARG;
+    DeviceGuard dg(h->device);
+    return launch_apply(h, 0, View<double, double>::lvl(h, 0), x, y, S(stream));
+}
+
+mg_status vcycle(mg_handle* h, const double* b, double* x, void* stream) {
+    if (!h || !b || !x || b == x) return MG_ERR_ARG;
+    DeviceGuard dg(h->device);
+    return run_vcycle(h, b, x, S(stream));
+}
+
+mg_status pressure_solve(mg_handle* h, const double* b, double* x, double tol, mg_solve_info* info,
+                         void* stream) {
+    if (!h || !b || !x || b == x || !(tol >= 0.0)) return MG_ERR_ARG;
+    DeviceGuard dg(h->device);
+    cudaStream_t s = S(stream);
+    const Lvl<double, double> L0 = View<double, double>::lvl(h, 0);
+    auto A = [&](const double* v, double* y) { return launch_apply(h, 0, L0, v, y, s); };
+    auto P = [&](const double* r, double* z) { return run_vcycle(h, r, z, s); };
+    return gcr(h, cells(h, 0), b, x, tol, info, s, A, P);
+}
+
+mg_status mixed_solve(mg_handle* h, const double* rhs_u, const double* rhs_p, double* u, double* p, double tol,
+                      mg_solve_info* info, void* stream) {
+    if (!h || !rhs_u || !rhs_p || !u || !p || !(tol >= 0.0)) return MG_ERR_ARG;
+    if (!h->mixed) return MG_ERR_UNSUPPORTED;
+    DeviceGuard dg(h->device);
+    cudaStream_t s = S(stream);
+    const size_t nu = (size_t)h->nu, np = cells(h, 0), n = nu + np;
+    // GCR runs on concatenated [u; p] vectors held by the handle
+    CK(cudaMemcpyAsync(h->mb, rhs_u, nu * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    CK(cudaMemcpyAsync(h->mb + nu, rhs_p, np * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    auto A = [&](const double* v, double* y) { return mixed_apply_impl(h, v, v + nu, y, y + nu, s); };
+    auto P = [&](const double* r, double* z) { return schur_impl(h, r, r + nu, z, z + nu, s); };
+    const mg_status st = gcr(h, n, h->mb, h->mx, tol, info, s, A, P);
+    if (st == MG_OK || st == MG_ERR_NOT_CONVERGED || st == MG_ERR_BREAKDOWN) {
+        CK(cudaMemcpyAsync(u, h->mx, nu * sizeof(double), cudaMemcpyDeviceToDevice, s));
+        CK(cudaMemcpyAsync(p, h->mx + nu, np * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    }
+    return st;
+}
+
+mg_status mg_level_apply(mg_handle* h, int32_t level, const double* x, double* y, void* stream) {
+    TRY(check_level(h, level));
+    if (!x || !y || x == y) return MG_ERR_ARG;
+    DeviceGuard dg(h->device);
+    return launch_apply(h, level, View<double, double>::lvl(h, level), x, y, S(stream));
+}
+
+mg_status mg_smooth(mg_handle* h, int32_t level, const double* b, const double* x_in, double* x_out,
+                    int32_t sweeps, void* stream) {
+    TRY(check_level(h, level));
+    if (!b || !x_out || sweeps < 0 || b == x_out) return MG_ERR_ARG;
+    DeviceGuard dg(h->device);
+    cudaStream_t s = S(stream);
+    DevLevel& d = h->lv[level];
+    const Lvl<double, double> L = View<double, double>::lvl(h, level);
+    const size_t n = cells(h, level);
+    const double* cur = x_in;
+    for (int i = 0; i < sweeps; ++i) {
+        double* dst = (cur == d.x64[0]) ? d.x64[1] : d.x64[0];
+        TRY((sweep_any<double, double, double, double>(h, level, L, cur, (const double*)nullptr, 0, b, nullptr, dst,
+                                                       h->prm.omega, s)));
+        cur = dst;
+    }
+    if (cur == nullptr) CK(cudaMemsetAsync(x_out, 0, n * sizeof(double), s));
+    else if (cur != x_out) CK(cudaMemcpyAsync(x_out, cur, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    return MG_OK;
+}
+
+mg_status mg_residual_restrict(mg_handle* h, int32_t level, const double* b, const double* x, double* bc,
+                               void* stream) {
+    TRY(check_level(h, level));
+    if (level + 1 >= h->L || !b || !x || !bc) return MG_ERR_ARG;
+    DeviceGuard dg(h->device);
+    return launch_restrict<double, double, false, double, double, double>(
+        h, level, View<double, double>::lvl(h, level), x, b, h->lv[level].w64, bc, h->lv[level + 1].ncol, S(stream));
+}
+
+mg_status mg_prolong_add(mg_handle* h, int32_t level, const double* xc, double* x, void* stream) {
+    TRY(check_level(h, level));
+    if (level + 1 >= h->L || !xc || !x) return MG_ERR_ARG;
+    DeviceGuard dg(h->device);
+    const DevLevel& d = h->lv[level];
+    return launch_prolong<double, false, double, double>(h, level, d.n, d.ncol, h->lv[level + 1].ncol, h->nlev, x, xc, x,
+                                                         S(stream));
+}
+
+mg_status mixed_apply(mg_handle* h, const double* u, const double* p, double* yu, double* yp, void* stream) {
+    if (!h || !u || !p || !yu || !yp) return MG_ERR_ARG;
+    if (!h->mixed) return MG_ERR_UNSUPPORTED;
+    DeviceGuard dg(h->device);
+    return mixed_apply_impl(h, u, p, yu, yp, S(stream));
+}
+
+mg_status schur_precond(mg_handle* h, const double* ru, const double* rp, double* u, double* p, void* stream) {
+    if (!h || !ru || !rp || !u || !p) return MG_ERR_ARG;
+    if (!h->mixed) return MG_ERR_UNSUPPORTED;
+    DeviceGuard dg(h->device);
+    return schur_impl(h, ru, rp, u, p, S(stream));
+}
+
+mg_status mg_profile_start(mg_handle* h, int32_t capacity) {
+    if (!h || capacity < 1 || capacity > (1 << 20)) return MG_ERR_ARG;
+    DeviceGuard dg(h->device);
+    while ((int)h->evpool.size() < 2 * capacity) {
+        cudaEvent_t e;
+        CK(cudaEventCreate(&e));
+        h->evpool.push_back(e);
+    }
+    h->recs.clear();
+    h->recs.reserve(capacity);
+    h->prof = true;
+    return MG_OK;
+}
+
+mg_status mg_profile_stop(mg_handle* h, mg_kernel_record* out, int32_t cap, int32_t* count) {
+    if (!h || !count || (cap > 0 && !out)) return MG_ERR_ARG;
+    DeviceGuard dg(h->device);
+    h->prof = false;
+    CK(cudaDeviceSynchronize());
+    const int n = (int)h->recs.size();
+    for (int i = 0; i < n && i < cap; ++i) {
+        float ms = 0.f;
+        CK(cudaEventElapsedTime(&ms, h->evpool[2 * i], h->evpool[2 * i + 1]));
+        out[i].kind = h->recs[i].kind;
+        out[i].level = h->recs[i].level;
+        out[i].bytes = h->recs[i].bytes;
+        out[i].ms = ms;
+    }
+    *count = n;
+    h->recs.clear();
+    return MG_OK;
+}
+
+}  // extern "C"
