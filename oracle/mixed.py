@@ -9,12 +9,16 @@ Test infrastructure only.  Follows Maynard, Melvin & Mueller (arXiv 2002.00756):
   after the elimination of rho (Step 1b) a 2x2 (u, p) system remains.  The reduced
   lowest-order system used here is, in strong volume-normalised form,
 
-      velocity row f:  (M-bar u)_f + (kappa_f / d_f) (p_R(f) - p_L(f)) = r_u,f
-      pressure row i:  p_i + (1 / V_i) sum_f sigma_if A_f u_f        = r_p,i
+      velocity row f:  (M-bar u)_f + (kappa_f / d_f) (p_R(f) - p_L(f))   = r_u,f
+      pressure row i:  p_i + (c_s dt / V_i) sum_f sigma_if A_f u_f        = r_p,i
 
-  with kappa_f = (c_s dt)^2 g_f, sigma_if = +1 when the face normal points out of cell
-  i.  M-bar = I + eps B_w, where B_w couples each interior vertical face to the interior
-  vertical faces directly above (weight beta_up) and below (beta_dn) in its column
+  with kappa_f = c_s dt g_f, sigma_if = +1 when the face normal points out of cell i.
+  Each coupling carries one factor of the time step (the linearised momentum and
+  pressure equations of Sec. 3.3, Eq. linear_continuum, each hold one tau dt), scaled by
+  the sound speed so that gradient and divergence are both O(CFL); their product gives
+  the Helmholtz coefficients (c_s dt)^2 g_f A_f / (V_i d_f).  M-bar = I + eps B_w, where
+  B_w couples each interior vertical face to the interior vertical faces directly above
+  (weight beta_up) and below (beta_dn) in its column
   (non-symmetric, the folded buoyancy term of Step 1a).  The top and bottom faces carry
   no flux: their rows are identity rows and they do not enter D or G.
 * Sec. 3.4: lumping M-bar to its row sums (diagonal M-ring) gives the Schur-complement
@@ -43,7 +47,7 @@ class MixedSystem:
         nlev, ncol = mesh.nlev, mesh.ncol
         self.nlev, self.ncol = nlev, ncol
         g = np.asarray(g, dtype=np.float64).reshape(nlev, ncol)
-        c2 = cs_dt * cs_dt
+        self.cs_dt = cs_dt
         self.L, self.R, side = mesh.hfaces()
         self.nhf = len(self.L)
         self.nh = nlev * self.nhf
@@ -53,12 +57,13 @@ class MixedSystem:
         ell = mesh.edge_len[side, self.L]
         dist = mesh.centre_dist[side, self.L]
         # gradient weights kappa_f / d_f and divergence weights A_f / V_i
-        self.kd_h = c2 * 0.5 * (g[:, self.L] + g[:, self.R]) / dist[None, :]   # (nlev, nhf)
-        self.div_hL = ell / mesh.area[self.L]                                 # (nhf,)
-        self.div_hR = ell / mesh.area[self.R]
+        self.kd_h = cs_dt * 0.5 * (g[:, self.L] + g[:, self.R]) / dist[None, :]   # (nlev, nhf)
+        self.div_hL = cs_dt * ell / mesh.area[self.L]                            # (nhf,)
+        self.div_hR = cs_dt * ell / mesh.area[self.R]
+        self.div_v = cs_dt / mesh.dz                                              # (nlev,)
         self.kd_v = np.zeros((nlev + 1, ncol))
         for kf in range(1, nlev):
-            self.kd_v[kf] = c2 * 0.5 * (g[kf - 1] + g[kf]) / mesh.dzc[kf]
+            self.kd_v[kf] = cs_dt * 0.5 * (g[kf - 1] + g[kf]) / mesh.dzc[kf]
         # velocity mass M-bar = I + eps B_w on vertical faces; couplings only between
         # interior faces of the same column
         interior = np.zeros(nlev + 1, dtype=bool)
@@ -91,13 +96,13 @@ class MixedSystem:
         return gh, gv
 
     def div(self, uh: np.ndarray, uv: np.ndarray) -> np.ndarray:
-        """D u in cells: (1 / V_i) sum_f sigma_if A_f u_f over the interior faces."""
+        """D u in cells: (c_s dt / V_i) sum_f sigma_if A_f u_f over the interior faces."""
         out = np.zeros((self.nlev, self.ncol))
         np.add.at(out, (slice(None), self.L), self.div_hL[None, :] * uh)
         np.add.at(out, (slice(None), self.R), -self.div_hR[None, :] * uh)
-        rdz = 1.0 / self.mesh.dz
-        out[:-1] += rdz[:-1, None] * uv[1:self.nlev]      # top face of cell k (faces 1..nlev-1)
-        out[1:] -= rdz[1:, None] * uv[1:self.nlev]        # bottom face of cell k (faces 1..nlev-1)
+        dv = self.div_v
+        out[:-1] += dv[:-1, None] * uv[1:self.nlev]       # top face of cell k (faces 1..nlev-1)
+        out[1:] -= dv[1:, None] * uv[1:self.nlev]         # bottom face of cell k (faces 1..nlev-1)
         return out
 
     def mass(self, uv: np.ndarray) -> np.ndarray:

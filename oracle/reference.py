@@ -66,9 +66,8 @@ def assemble_mixed(S: MixedSystem) -> sp.csr_matrix:
     put(pp, pp, 1.0)
     put(pp[:, S.L], uh, S.div_hL[None, :])
     put(pp[:, S.R], uh, -S.div_hR[None, :])
-    rdz = 1.0 / S.mesh.dz
-    put(pp[:-1], uv[1:nlev], rdz[:-1, None])
-    put(pp[1:], uv[1:nlev], -rdz[1:, None])
+    put(pp[:-1], uv[1:nlev], S.div_v[:-1, None])
+    put(pp[1:], uv[1:nlev], -S.div_v[1:, None])
     n = S.nu + S.np
     A = sp.coo_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))),
                       shape=(n, n))

@@ -144,13 +144,13 @@ struct MixedDev {
     const int32_t* faceL;           // [nfh]
     const int32_t* faceR;           // [nfh]
     const int32_t* fof;             // [4][ncol]
-    const double* sdiv;             // [4][ncol] +-(edge length / area), + if the column owns the face
-    const double* kd_h;             // [nlev][nfh]   kappa_f / d_f
+    const double* sdiv;             // [4][ncol] +-c_s dt (edge length / area), + if the column owns the face
+    const double* kd_h;             // [nlev][nfh]   kappa_f / d_f, kappa_f = c_s dt g_f
     const double* kd_v;             // [nlev+1][ncol]
     const double* w_up;             // [nlev+1][ncol] eps beta_up (interior couplings only)
     const double* w_dn;             // [nlev+1][ncol]
     const double* mlump;            // [nlev+1][ncol] row sums of M-bar
-    const double* rdz;              // [nlev]
+    const double* divv;             // [nlev] c_s dt / dz
 };
 
 // (D u)_i, vertical velocities optionally divided by the lumped mass
@@ -171,7 +171,7 @@ __device__ __forceinline__ double div_cell(const MixedDev& M, int k, int c, cons
         const size_t o = (size_t)k * ncol + c;
         v -= LUMP ? __ldg(uv + o) / __ldg(M.mlump + o) : __ldg(uv + o);
     }
-    return s + __ldg(M.rdz + k) * v;
+    return s + __ldg(M.divv + k) * v;
 }
 
 // velocity rows on horizontal faces: yh = uh + kd (p_R - p_L)   [MODE 0]

@@ -578,25 +578,29 @@ mg_status setup_impl(mg_handle* h, const mg_mesh* mesh, const mg_params* prm, co
     if (h->mixed) {
         const mg::HGeom& G = hg[0];
         const int nfh = 2 * ncol0;
-        const double c2 = mesh->cs_dt * mesh->cs_dt;
-        std::vector<double> kd_h((size_t)nlev * nfh), kd_v(NV0, 0.0), sdiv(4 * (size_t)ncol0);
+        // gradient and divergence each carry one factor c_s dt; their product is the
+        // Helmholtz coupling (c_s dt)^2 g_f A_f / (V_i d_f)
+        const double c = mesh->cs_dt;
+        std::vector<double> kd_h((size_t)nlev * nfh), kd_v(NV0, 0.0), sdiv(4 * (size_t)ncol0), divv(nlev);
+        for (int k = 0; k < nlev; ++k) divv[k] = c / vg.dz[k];
         for (int f = 0; f < nfh; ++f) {
             const int Lc = G.faceL[f], Rc = G.faceR[f], sd = G.faceSide[f];
             const double dist = G.cdist[sd * ncol0 + Lc];
             for (int k = 0; k < nlev; ++k)
-                kd_h[(size_t)k * nfh + f] = c2 * 0.5 * (g[(size_t)k * ncol0 + Lc] + g[(size_t)k * ncol0 + Rc]) / dist;
+                kd_h[(size_t)k * nfh + f] = c * 0.5 * (g[(size_t)k * ncol0 + Lc] + g[(size_t)k * ncol0 + Rc]) / dist;
         }
         for (int kf = 1; kf < nlev; ++kf)
-            for (int c = 0; c < ncol0; ++c)
-                kd_v[(size_t)kf * ncol0 + c] = c2 * 0.5 * (g[(size_t)(kf - 1) * ncol0 + c] + g[(size_t)kf * ncol0 + c]) / vg.dzc[kf];
-        for (int c = 0; c < ncol0; ++c)
+            for (int col = 0; col < ncol0; ++col)
+                kd_v[(size_t)kf * ncol0 + col] =
+                    c * 0.5 * (g[(size_t)(kf - 1) * ncol0 + col] + g[(size_t)kf * ncol0 + col]) / vg.dzc[kf];
+        for (int col = 0; col < ncol0; ++col)
             for (int sd = 0; sd < 4; ++sd) {
-                const int f = G.face_of[sd * ncol0 + c];
-                const double sgn = (G.faceL[f] == c) ? 1.0 : -1.0;
-                sdiv[(size_t)sd * ncol0 + c] = sgn * G.edge_len[sd * ncol0 + c] / G.area[c];
+                const int f = G.face_of[sd * ncol0 + col];
+                const double sgn = (G.faceL[f] == col) ? 1.0 : -1.0;
+                sdiv[(size_t)sd * ncol0 + col] = sgn * c * G.edge_len[sd * ncol0 + col] / G.area[col];
             }
         int32_t *fL, *fR;
-        double *dkd_h, *dkd_v, *dsdiv, *dwu, *dwd, *dml;
+        double *dkd_h, *dkd_v, *dsdiv, *dwu, *dwd, *dml, *ddivv;
         TRY(upload(h, &fL, G.faceL));
         TRY(upload(h, &fR, G.faceR));
         TRY(upload(h, &dkd_h, kd_h));
@@ -605,7 +609,8 @@ mg_status setup_impl(mg_handle* h, const mg_mesh* mesh, const mg_params* prm, co
         TRY(upload(h, &dwu, w_up));
         TRY(upload(h, &dwd, w_dn));
         TRY(upload(h, &dml, mlump));
-        h->md = mg::MixedDev{ncol0, nlev, nfh, fL, fR, h->lv[0].fof, dsdiv, dkd_h, dkd_v, dwu, dwd, dml, h->rdz64};
+        TRY(upload(h, &ddivv, divv));
+        h->md = mg::MixedDev{ncol0, nlev, nfh, fL, fR, h->lv[0].fof, dsdiv, dkd_h, dkd_v, dwu, dwd, dml, ddivv};
         h->nu = (int64_t)nlev * nfh + (int64_t)NV0;
         TRY(dalloc(h, &h->schurB, N0));
         TRY(dalloc(h, &h->mb, (size_t)h->nu + N0));

@@ -106,8 +106,16 @@ def test_block_jacobi_sweeps(mg, name, sweeps, start):
         out = torch.empty(n, dtype=torch.float64, device="cuda")
         mg.mg_smooth(h, l, dev(b), None if start == "zero" else dev(x0), out, sweeps)
         ref = H.jacobi(b, x0, cfg.omega, sweeps).ravel()
-        err = np.linalg.norm(host(out) - ref) / np.linalg.norm(ref)
-        assert err < 1e-12, (l, err)
+        # rounding of b - H x (terms up to CFL_v^2 |x|) reaches the result through
+        # Hz^{-1}, whose gain on the vertically smooth mode is O(1): propagate the
+        # summation-order bound of every sweep's residual through Hz^{-1} (an M-matrix,
+        # so |Hz^{-1} e| <= Hz^{-1} |e|)
+        bound, xi = 1e-12 * np.linalg.norm(ref), x0
+        for _ in range(sweeps):
+            s = abs_apply_scale(H, xi) + np.abs(b)
+            bound += 32 * np.finfo(float).eps * cfg.omega * np.linalg.norm(H.hz_solve(s))
+            xi = H.jacobi(b, xi, cfg.omega, 1)
+        assert np.linalg.norm(host(out) - ref) <= bound, (l, np.linalg.norm(host(out) - ref), bound)
 
 
 @pytest.mark.parametrize("name", ["c12", "c20l9", "c4l1"])

@@ -50,7 +50,7 @@ def test_boundary_faces_are_identity_rows():
 
 
 def test_discrete_integration_by_parts():
-    # sum_f (A_f d_f / kappa_f) (G p)_f u_f = - sum_i V_i p_i (D u)_i  (G = -D^T up to weights)
+    # c_s dt sum_f (A_f d_f / kappa_f) (G p)_f u_f = - sum_i V_i p_i (D u)_i  (G = -D^T up to weights)
     S, inp, _ = _system()
     m = S.mesh
     rng = np.random.default_rng(1)
@@ -64,7 +64,7 @@ def test_discrete_integration_by_parts():
     w_h = A_h / S.kd_h                               # A_f d_f / kappa_f
     w_v = np.zeros_like(gv)
     w_v[1:-1] = m.area[None, :] / S.kd_v[1:-1]
-    lhs = np.sum(w_h * gh * uh) + np.sum(w_v * gv * uv)
+    lhs = S.cs_dt * (np.sum(w_h * gh * uh) + np.sum(w_v * gv * uv))
     V = m.dz[:, None] * m.area[None, :]
     rhs = -np.sum(V * p * S.div(uh, uv))
     assert lhs == pytest.approx(rhs, rel=1e-11)
