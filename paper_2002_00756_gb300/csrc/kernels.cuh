@@ -111,10 +111,26 @@ __global__ void __launch_bounds__(256) k_apply(Lvl<T, C> L, const X* __restrict_
 // subtraction), stashing y_k / p_k and a_up_k / p_k in shared memory; the backward
 // pass substitutes and writes x_out.  Optionally copies b into `bcopy` (entry of the
 // FP32 V-cycle, where b arrives in FP64).
-template <typename T, typename C, int MODE, typename X, typename B, typename O, bool BCOPY>
+//
+// Latency hiding: the loads of level k + PF are issued before level k is computed, into a
+// register ring of PF levels (the loop over k is unrolled by PF so the ring is indexed
+// statically); the elimination recurrence then never waits on memory.
+template <typename T, typename X, bool PRO>
+struct SweepLv {
+    T xp;                   // own column, level k+1 (raw iterate)
+    T xn[4];                // E, W, N, S neighbours, level k (raw iterate)
+    T cp, cn[4];            // prolongation terms (PRO only)
+    T th[4];                // horizontal face coefficients
+    T tup;                  // vertical face above
+    T b;
+};
+
+template <typename T, typename C, int MODE, typename X, typename B, typename O, bool BCOPY, int PF>
 __global__ void k_sweep(Lvl<T, C> L, const X* __restrict__ x, const T* __restrict__ xc,
                         int ncol_c, const B* __restrict__ b, T* __restrict__ bcopy,
                         O* __restrict__ xo, T omega) {
+    constexpr bool PRO = (MODE == XM_PROLONG || MODE == XM_PROLONG0);
+    constexpr bool RAW = (MODE == XM_PLAIN || MODE == XM_PROLONG);   // reads the fine iterate
     extern __shared__ unsigned char smem_raw[];
     T* sc = reinterpret_cast<T*>(smem_raw);
     T* se = sc + (size_t)L.nlev * blockDim.x;
@@ -128,50 +144,89 @@ __global__ void k_sweep(Lvl<T, C> L, const X* __restrict__ x, const T* __restric
         nb[s] = __ldg(L.nbr + s * ncol + c);
         fo[s] = __ldg(L.fof + s * ncol + c);
     }
-    if (MODE == XM_PROLONG || MODE == XM_PROLONG0) {
+    if (PRO) {
         pc = parent_col(c, L.n);
 #pragma unroll
         for (int s = 0; s < 4; ++s) pn[s] = parent_col(nb[s], L.n);
     }
     const T rA = __ldg(L.rA + c);
-    T xm = T(0), x0 = xval<MODE, T>(x, xc, 0, 0, c, pc), tdn = T(0);
-    T q = T(0), ip = T(0), y = T(0);
-    for (int k = 0; k < nlev; ++k) {
+
+    auto load = [&](int k, SweepLv<T, X, PRO>& d) {
         const size_t o = (size_t)k * ncol, oc = (size_t)k * ncol_c;
-        const T xp = (k + 1 < nlev) ? xval<MODE, T>(x, xc, o + ncol, oc + ncol_c, c, pc) : T(0);
-        const T tup = ldc<T>(L.Tv + o + ncol + c);
-        const C* th = L.Th + (size_t)k * nf;
-        const T te = ldc<T>(th + fo[0]), tw = ldc<T>(th + fo[1]);
-        const T tn = ldc<T>(th + fo[2]), ts = ldc<T>(th + fo[3]);
-        T hx = T(0);
-        if (MODE != XM_ZERO) {
-            hx = te * (x0 - xval<MODE, T>(x, xc, o, oc, nb[0], pn[0]));
-            hx += tw * (x0 - xval<MODE, T>(x, xc, o, oc, nb[1], pn[1]));
-            hx += tn * (x0 - xval<MODE, T>(x, xc, o, oc, nb[2], pn[2]));
-            hx += ts * (x0 - xval<MODE, T>(x, xc, o, oc, nb[3], pn[3]));
+        const bool up = k + 1 < nlev;
+        if (RAW) {
+            d.xp = up ? ldx<T>(x + o + ncol + c) : T(0);
+#pragma unroll
+            for (int s = 0; s < 4; ++s) d.xn[s] = ldx<T>(x + o + nb[s]);
         }
-        const T rdz = __ldg(L.rdz + k);
-        const T bk = (T)__ldg(b + o + c);
-        if (BCOPY) bcopy[o + c] = bk;
-        T r = bk;
-        if (MODE != XM_ZERO) r -= x0 + (rA * hx + rdz * (tup * (x0 - xp) + tdn * (x0 - xm)));
-        const T aup = rdz * tup, adn = rdz * tdn;
-        const T m = adn * ip;
-        q = (T(1) + rA * ((te + tw) + (tn + ts))) + m * q;
-        const T p = q + aup;
-        y = r + m * y;
-        ip = T(1) / p;
-        sc[(size_t)k * bd + tid] = y * ip;
-        se[(size_t)k * bd + tid] = aup * ip;
-        xm = x0;
-        x0 = xp;
-        tdn = tup;
+        if (PRO) {
+            d.cp = up ? __ldg(xc + oc + ncol_c + pc) : T(0);
+#pragma unroll
+            for (int s = 0; s < 4; ++s) d.cn[s] = __ldg(xc + oc + pn[s]);
+        }
+        const C* th = L.Th + (size_t)k * nf;
+#pragma unroll
+        for (int s = 0; s < 4; ++s) d.th[s] = ldc<T>(th + fo[s]);
+        d.tup = ldc<T>(L.Tv + o + ncol + c);
+        d.b = (T)__ldg(b + o + c);
+    };
+
+    SweepLv<T, X, PRO> ring[PF];
+#pragma unroll
+    for (int j = 0; j < PF; ++j)
+        if (j < nlev) load(j, ring[j]);
+    T xm = T(0), x0 = T(0), tdn = T(0);
+    if (RAW) x0 = ldx<T>(x + c);
+    if (PRO) x0 += __ldg(xc + pc);
+    T q = T(0), ip = T(0), y = T(0);
+    for (int k0 = 0; k0 < nlev; k0 += PF) {
+#pragma unroll
+        for (int j = 0; j < PF; ++j) {
+            const int k = k0 + j;
+            if (k < nlev) {
+                const SweepLv<T, X, PRO> d = ring[j];
+                if (k + PF < nlev) load(k + PF, ring[j]);
+                T xp = T(0), xe[4] = {T(0), T(0), T(0), T(0)};
+                if (RAW) {
+                    xp = d.xp;
+#pragma unroll
+                    for (int s = 0; s < 4; ++s) xe[s] = d.xn[s];
+                }
+                if (PRO) {
+                    xp += d.cp;
+#pragma unroll
+                    for (int s = 0; s < 4; ++s) xe[s] += d.cn[s];
+                }
+                const T rdz = __ldg(L.rdz + k);
+                if (BCOPY) bcopy[(size_t)k * ncol + c] = d.b;
+                T r = d.b;
+                if (MODE != XM_ZERO) {
+                    T hx = d.th[0] * (x0 - xe[0]);
+                    hx += d.th[1] * (x0 - xe[1]);
+                    hx += d.th[2] * (x0 - xe[2]);
+                    hx += d.th[3] * (x0 - xe[3]);
+                    r -= x0 + (rA * hx + rdz * (d.tup * (x0 - xp) + tdn * (x0 - xm)));
+                }
+                const T aup = rdz * d.tup, adn = rdz * tdn;
+                const T m = adn * ip;
+                q = (T(1) + rA * ((d.th[0] + d.th[1]) + (d.th[2] + d.th[3]))) + m * q;
+                const T p = q + aup;
+                y = r + m * y;
+                ip = T(1) / p;
+                sc[(size_t)k * bd + tid] = y * ip;
+                se[(size_t)k * bd + tid] = aup * ip;
+                xm = x0;
+                x0 = xp;
+                tdn = d.tup;
+            }
+        }
     }
-    T d = T(0);
+    T dlt = T(0);
+#pragma unroll 4
     for (int k = nlev - 1; k >= 0; --k) {
-        d = sc[(size_t)k * bd + tid] + se[(size_t)k * bd + tid] * d;
+        dlt = sc[(size_t)k * bd + tid] + se[(size_t)k * bd + tid] * dlt;
         const size_t o = (size_t)k * ncol, oc = (size_t)k * ncol_c;
-        xo[o + c] = (O)(xval<MODE, T>(x, xc, o, oc, c, pc) + omega * d);
+        xo[o + c] = (O)(xval<MODE, T>(x, xc, o, oc, c, pc) + omega * dlt);
     }
 }
 

@@ -9,10 +9,20 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "kernels.cuh"
+
 namespace mg {
 
 constexpr int RED_THREADS = 256;
 constexpr int MAXR = 16;   // maximum GCR restart length (MG_MAX_RESTART)
+
+// device scalar block of the GCR iteration
+struct GcrScal {
+    double beta[MAXR * MAXR];   // beta[j * MAXR + i]: w_j orthogonalised against w_i, i < j
+    double alpha[MAXR];         // step length of direction j
+    double ww[MAXR];            // <w_i, w_i> of the orthogonalised directions
+    double rr, bb;              // <r, r>, <b, b>
+};
 
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
@@ -20,13 +30,17 @@ __device__ __forceinline__ double warp_sum(double v) {
     return v;
 }
 
-// Sums v[0..ND) over the whole grid; returns true in the one block that holds the totals,
-// which thread 0 finds in `result`.
+// Sums v[0..ND) over the whole grid (any 1-D or 2-D grid of RED_THREADS-thread blocks).
+// Each block writes its ND partial sums; the last block to finish (ticket counter, no
+// waiting) adds all partials with every thread taking a fixed stride of blocks, then a
+// fixed tree; thread 0 of that block gets the totals in `tot` and the function returns
+// true there.  The order of every addition is fixed, so results are bitwise repeatable.
 template <int ND>
-__device__ bool grid_reduce(double (&v)[ND], double* partials, unsigned int* ticket, double* result) {
+__device__ bool grid_reduce(double (&v)[ND], double* partials, unsigned int* ticket, double (&tot)[ND]) {
     __shared__ double sm[ND][RED_THREADS / 32];
     __shared__ bool last;
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const unsigned nblk = gridDim.x * gridDim.y, bid = blockIdx.y * gridDim.x + blockIdx.x;
 #pragma unroll
     for (int i = 0; i < ND; ++i) v[i] = warp_sum(v[i]);
     if (lane == 0) {
@@ -36,105 +50,148 @@ __device__ bool grid_reduce(double (&v)[ND], double* partials, unsigned int* tic
     __syncthreads();
     if (threadIdx.x < ND) {
         double s = 0.0;
-        for (int w = 0; w < nw; ++w) s += sm[threadIdx.x][w];
-        partials[(size_t)blockIdx.x * ND + threadIdx.x] = s;
+        for (int w = 0; w < RED_THREADS / 32; ++w) s += sm[threadIdx.x][w];
+        partials[(size_t)bid * ND + threadIdx.x] = s;
     }
     __threadfence();
     __syncthreads();
-    if (threadIdx.x == 0) last = (atomicAdd(ticket, 1u) == gridDim.x - 1);
+    if (threadIdx.x == 0) last = (atomicAdd(ticket, 1u) == nblk - 1);
     __syncthreads();
     if (!last) return false;
     __threadfence();
-    if (threadIdx.x < ND) {
-        double s = 0.0;
-        for (unsigned b = 0; b < gridDim.x; ++b) s += __ldcg(partials + (size_t)b * ND + threadIdx.x);
-        result[threadIdx.x] = s;
+    double a[ND];
+#pragma unroll
+    for (int i = 0; i < ND; ++i) a[i] = 0.0;
+    for (unsigned b = threadIdx.x; b < nblk; b += RED_THREADS) {
+#pragma unroll
+        for (int i = 0; i < ND; ++i) a[i] += __ldcg(partials + (size_t)b * ND + i);
     }
-    if (threadIdx.x == 0) *ticket = 0u;
+#pragma unroll
+    for (int i = 0; i < ND; ++i) a[i] = warp_sum(a[i]);
     __syncthreads();
-    return true;
+    if (lane == 0) {
+#pragma unroll
+        for (int i = 0; i < ND; ++i) sm[i][wid] = a[i];
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int i = 0; i < ND; ++i) {
+            double s = 0.0;
+            for (int w = 0; w < RED_THREADS / 32; ++w) s += sm[i][w];
+            tot[i] = s;
+        }
+        *ticket = 0u;
+    }
+    return threadIdx.x == 0;
 }
 
-// sc[0] = <a, b>
+// out = <a, b>
 __global__ void __launch_bounds__(RED_THREADS) k_dot(size_t n, const double* __restrict__ a,
                                                      const double* __restrict__ b, double* partials,
-                                                     unsigned int* ticket, double* sc) {
-    double v[1] = {0.0};
+                                                     unsigned int* ticket, double* out) {
+    double v[1] = {0.0}, t[1];
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
         v[0] += a[i] * b[i];
-    grid_reduce<1>(v, partials, ticket, sc);
+    if (grid_reduce<1>(v, partials, ticket, t)) *out = t[0];
 }
 
-// dots[j] = <w, W_j>, j < s  (classical Gram-Schmidt coefficients, one pass over w)
-__global__ void __launch_bounds__(RED_THREADS) k_gcr_dots(size_t n, const double* __restrict__ w,
-                                                          const double* __restrict__ Wb, size_t ld, int s,
-                                                          double* partials, unsigned int* ticket,
-                                                          double* dots) {
-    double v[MAXR];
-#pragma unroll
-    for (int j = 0; j < MAXR; ++j) v[j] = 0.0;
-    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
-        const double wi = w[i];
-#pragma unroll
-        for (int j = 0; j < MAXR; ++j)
-            if (j < s) v[j] += wi * __ldg(Wb + (size_t)j * ld + i);
+// GCR step coefficients for direction j (classical Gram-Schmidt, one pass):
+//   beta_i = <w, w_i> / <w_i, w_i>,  <w', w'> = <w, w> - sum_i beta_i <w, w_i>,
+//   <r, w'> = <r, w> - sum_i beta_i <r, w_i>,  alpha = <r, w'> / <w', w'>,
+// with sums = [<w, w_i> (JM), <r, w_i> (JM), <w, w>, <r, w>].
+template <int JM>
+__device__ void gcr_coeffs(int j, const double (&t)[2 * JM + 2], GcrScal* S) {
+    double ww = t[2 * JM], rw = t[2 * JM + 1];
+    for (int i = 0; i < j; ++i) {
+        const double beta = t[i] / S->ww[i];
+        S->beta[j * MAXR + i] = beta;
+        ww -= beta * t[i];
+        rw -= beta * t[JM + i];
     }
-    grid_reduce<MAXR>(v, partials, ticket, dots);
+    S->alpha[j] = rw / ww;
 }
 
-// w -= sum_j beta_j W_j, z -= sum_j beta_j Z_j, beta_j = dots[j] / ww[j]; then
-// ww[s] = <w, w> and alpha = <r, w> / <w, w>.
-__global__ void __launch_bounds__(RED_THREADS) k_gcr_orth(size_t n, double* __restrict__ w,
-                                                          double* __restrict__ z,
-                                                          const double* __restrict__ Wb,
-                                                          const double* __restrict__ Zb, size_t ld, int s,
-                                                          const double* __restrict__ dots, double* ww,
+// Accumulates the GCR sums of one element: w_e, r_e and the stored directions W_i[e].
+template <int JM>
+__device__ __forceinline__ void gcr_accumulate(double (&v)[2 * JM + 2], double we, double re,
+                                               const double* __restrict__ Wb, size_t ld, size_t e, int j) {
+#pragma unroll
+    for (int i = 0; i < JM; ++i) {
+        if (i < j) {
+            const double wi = __ldg(Wb + (size_t)i * ld + e);
+            v[i] += we * wi;
+            v[JM + i] += re * wi;
+        }
+    }
+    v[2 * JM] += we * we;
+    v[2 * JM + 1] += re * we;
+}
+
+// GCR sums for a new direction w (mixed system path, where w comes from other kernels).
+template <int JM>
+__global__ void __launch_bounds__(RED_THREADS) k_gcr_sums(size_t n, const double* __restrict__ w,
+                                                          const double* __restrict__ Wb, size_t ld, int j,
                                                           const double* __restrict__ r, double* partials,
-                                                          unsigned int* ticket, double* tmp2,
-                                                          double* alpha) {
+                                                          unsigned int* ticket, GcrScal* S) {
+    double v[2 * JM + 2], t[2 * JM + 2];
+#pragma unroll
+    for (int i = 0; i < 2 * JM + 2; ++i) v[i] = 0.0;
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x)
+        gcr_accumulate<JM>(v, __ldg(w + e), __ldg(r + e), Wb, ld, e, j);
+    if (grid_reduce<2 * JM + 2>(v, partials, ticket, t)) gcr_coeffs<JM>(j, t, S);
+}
+
+// w_j <- w_j - sum_i beta_i w_i (stored in place), r <- r - alpha_j w_j,
+// then <w_j, w_j> -> ww[j] and <r, r> -> rr.
+__global__ void __launch_bounds__(RED_THREADS) k_gcr_orth_update(size_t n, double* __restrict__ Wb, size_t ld,
+                                                                 int j, double* __restrict__ r,
+                                                                 double* partials, unsigned int* ticket,
+                                                                 GcrScal* S) {
     double beta[MAXR];
 #pragma unroll
-    for (int j = 0; j < MAXR; ++j) beta[j] = (j < s) ? dots[j] / ww[j] : 0.0;
-    double v[2] = {0.0, 0.0};
-    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
-        double wi = w[i], zi = z[i];
+    for (int i = 0; i < MAXR; ++i) beta[i] = (i < j) ? S->beta[j * MAXR + i] : 0.0;
+    const double a = S->alpha[j];
+    double* w = Wb + (size_t)j * ld;
+    double v[2] = {0.0, 0.0}, t[2];
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
+        double we = w[e];
 #pragma unroll
-        for (int j = 0; j < MAXR; ++j) {
-            if (j < s) {
-                wi -= beta[j] * __ldg(Wb + (size_t)j * ld + i);
-                zi -= beta[j] * __ldg(Zb + (size_t)j * ld + i);
-            }
-        }
-        if (s > 0) {
-            w[i] = wi;
-            z[i] = zi;
-        }
-        v[0] += wi * wi;
-        v[1] += __ldg(r + i) * wi;
+        for (int i = 0; i < MAXR; ++i)
+            if (i < j) we -= beta[i] * __ldg(Wb + (size_t)i * ld + e);
+        if (j > 0) w[e] = we;
+        const double re = r[e] - a * we;
+        r[e] = re;
+        v[0] += we * we;
+        v[1] += re * re;
     }
-    if (grid_reduce<2>(v, partials, ticket, tmp2) && threadIdx.x == 0) {
-        ww[s] = tmp2[0];
-        *alpha = tmp2[1] / tmp2[0];
+    if (grid_reduce<2>(v, partials, ticket, t)) {
+        S->ww[j] = t[0];
+        S->rr = t[1];
     }
 }
 
-// x += alpha z, r -= alpha w, rr = <r, r>
-__global__ void __launch_bounds__(RED_THREADS) k_gcr_update(size_t n, double* __restrict__ x,
-                                                            double* __restrict__ r,
-                                                            const double* __restrict__ z,
-                                                            const double* __restrict__ w,
-                                                            const double* __restrict__ alpha,
-                                                            double* partials, unsigned int* ticket,
-                                                            double* rr) {
-    const double a = *alpha;
-    double v[1] = {0.0};
-    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
-        x[i] += a * __ldg(z + i);
-        const double ri = r[i] - a * __ldg(w + i);
-        r[i] = ri;
-        v[0] += ri * ri;
+// x += sum_{i <= jl} gamma_i z_i with the raw (not orthogonalised) directions z_i:
+// x = sum_i alpha_i zhat_i, zhat_i = z_i - sum_{m<i} beta_im zhat_m, unrolled from the top.
+__global__ void k_gcr_xupdate(size_t n, double* __restrict__ x, const double* __restrict__ Zb, size_t ld, int jl,
+                              const GcrScal* __restrict__ S) {
+    __shared__ double g[MAXR];
+    if (threadIdx.x == 0) {
+        double a[MAXR];
+        for (int i = 0; i <= jl; ++i) a[i] = S->alpha[i];
+        for (int i = jl; i >= 0; --i) {
+            g[i] = a[i];
+            for (int m = 0; m < i; ++m) a[m] -= a[i] * S->beta[i * MAXR + m];
+        }
     }
-    grid_reduce<1>(v, partials, ticket, rr);
+    __syncthreads();
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
+        double xe = x[e];
+#pragma unroll
+        for (int i = 0; i < MAXR; ++i)
+            if (i <= jl) xe += g[i] * __ldg(Zb + (size_t)i * ld + e);
+        x[e] = xe;
+    }
 }
 
 // ---------------------------------------------------------------------------------------
@@ -219,6 +276,52 @@ __global__ void k_mx_cells(MixedDev M, const double* __restrict__ uh, const doub
     const size_t o = (size_t)k * M.ncol + c;
     if (MODE == 0) yp[o] = __ldg(p + o) + div_cell<false>(M, k, c, uh, uv);
     else yp[o] = __ldg(p + o) - div_cell<true>(M, k, c, uh, uv);
+}
+
+// Pressure-system GCR pass 1: w = H z (FP64, Eq. helmholtz_operator) for the levels
+// [k0, k0 + kchunk) of one column per thread, fused with the GCR sums of the new direction.
+template <int JM>
+__global__ void __launch_bounds__(RED_THREADS) k_apply_gcr(Lvl<double, double> L, const double* __restrict__ z,
+                                                           double* __restrict__ w, const double* __restrict__ Wb,
+                                                           size_t ld, int j, const double* __restrict__ r,
+                                                           int kchunk, double* partials, unsigned int* ticket,
+                                                           GcrScal* S) {
+    double v[2 * JM + 2], t[2 * JM + 2];
+#pragma unroll
+    for (int i = 0; i < 2 * JM + 2; ++i) v[i] = 0.0;
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c < L.ncol) {
+        const size_t ncol = L.ncol, nf = 2 * ncol;
+        const int k0 = blockIdx.y * kchunk;
+        const int k1 = min(L.nlev, k0 + kchunk);
+        int nb[4], fo[4];
+#pragma unroll
+        for (int s = 0; s < 4; ++s) {
+            nb[s] = __ldg(L.nbr + s * ncol + c);
+            fo[s] = __ldg(L.fof + s * ncol + c);
+        }
+        const double rA = __ldg(L.rA + c);
+        double xm = k0 > 0 ? __ldg(z + (size_t)(k0 - 1) * ncol + c) : 0.0;
+        double x0 = __ldg(z + (size_t)k0 * ncol + c);
+        double tdn = __ldg(L.Tv + (size_t)k0 * ncol + c);
+        for (int k = k0; k < k1; ++k) {
+            const size_t o = (size_t)k * ncol;
+            const double xp = (k + 1 < L.nlev) ? __ldg(z + o + ncol + c) : 0.0;
+            const double tup = __ldg(L.Tv + o + ncol + c);
+            const double* th = L.Th + (size_t)k * nf;
+            double h = __ldg(th + fo[0]) * (x0 - __ldg(z + o + nb[0]));
+            h += __ldg(th + fo[1]) * (x0 - __ldg(z + o + nb[1]));
+            h += __ldg(th + fo[2]) * (x0 - __ldg(z + o + nb[2]));
+            h += __ldg(th + fo[3]) * (x0 - __ldg(z + o + nb[3]));
+            const double we = x0 + (rA * h + __ldg(L.rdz + k) * (tup * (x0 - xp) + tdn * (x0 - xm)));
+            w[o + c] = we;
+            gcr_accumulate<JM>(v, we, __ldg(r + o + c), Wb, ld, o + c, j);
+            xm = x0;
+            x0 = xp;
+            tdn = tup;
+        }
+    }
+    if (grid_reduce<2 * JM + 2>(v, partials, ticket, t)) gcr_coeffs<JM>(j, t, S);
 }
 
 }  // namespace mg

@@ -59,8 +59,9 @@ struct mg_handle {
     double* Z = nullptr;        // [restart][glen]
     double* W = nullptr;        // [restart][glen]
     double* r = nullptr;        // [glen]
-    double* sc = nullptr;       // device scalars
+    mg::GcrScal* gs = nullptr;  // device scalars of the GCR iteration
     double* partials = nullptr;
+    size_t npartials = 0;
     unsigned int* tickets = nullptr;
     double* host_sc = nullptr;  // pinned
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
@@ -85,9 +86,11 @@ struct mg_handle {
 
 namespace {
 
-// device scalar slots
-enum { SC_DOTS = 0, SC_WW = SC_DOTS + mg::MAXR, SC_ALPHA = SC_WW + mg::MAXR, SC_RR, SC_BB, SC_TMP, SC_COUNT = SC_TMP + 4 };
-enum { TK_DOT = 0, TK_DOTS, TK_ORTH, TK_UPD, TK_COUNT };
+enum { TK_DOT = 0, TK_SUMS, TK_ORTH, TK_COUNT };
+
+// k-chunk of the column kernels that have no vertical recurrence (apply): short chunks give
+// many independent threads, so the loads of different threads overlap
+constexpr int APPLY_KCHUNK = 8;
 
 #define CK(call)                                   \
     do {                                           \
@@ -211,14 +214,18 @@ mg_status launch_apply(mg_handle* h, int lev, const Lvl<T, C>& L, const X* x, Y*
     const double nc = (double)L.nlev * L.ncol;
     Prof pr(h, MG_K_APPLY, lev, nc * (sizeof(X) + 3 * sizeof(C) + sizeof(Y)), s);
     const int bd = 128;
-    const long target = 4L * 152 * 256;
-    int kc = (int)((long)L.nlev * L.ncol / target);
-    kc = kc < 4 ? 4 : (kc > L.nlev ? L.nlev : kc);
+    const int kc = APPLY_KCHUNK;
     dim3 grid((L.ncol + bd - 1) / bd, (L.nlev + kc - 1) / kc);
     mg::k_apply<T, C, X, Y><<<grid, bd, 0, s>>>(L, x, y, kc);
     CK(cudaGetLastError());
     return MG_OK;
 }
+
+// prefetch depth of the sweep's register ring (levels in flight per thread)
+template <typename T>
+struct SweepPF {
+    static constexpr int value = sizeof(T) == 8 ? 2 : 4;
+};
 
 template <typename T, typename C, int MODE, typename X, typename B, typename O, bool BCOPY>
 mg_status launch_sweep(mg_handle* h, int lev, const Lvl<T, C>& L, const X* x, const T* xc, int ncol_c,
@@ -236,10 +243,11 @@ mg_status launch_sweep(mg_handle* h, int lev, const Lvl<T, C>& L, const X* x, co
     if (bd > cap) bd = cap;
     const size_t smem = 2 * (size_t)L.nlev * bd * sizeof(T);
     if (smem > 48 * 1024)
-        CK(cudaFuncSetAttribute(mg::k_sweep<T, C, MODE, X, B, O, BCOPY>,
+        CK(cudaFuncSetAttribute(mg::k_sweep<T, C, MODE, X, B, O, BCOPY, SweepPF<T>::value>,
                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     const int grid = (L.ncol + bd - 1) / bd;
-    mg::k_sweep<T, C, MODE, X, B, O, BCOPY><<<grid, bd, smem, s>>>(L, x, xc, ncol_c, b, bcopy, xo, (T)omega);
+    mg::k_sweep<T, C, MODE, X, B, O, BCOPY, SweepPF<T>::value><<<grid, bd, smem, s>>>(L, x, xc, ncol_c, b, bcopy,
+                                                                                     xo, (T)omega);
     CK(cudaGetLastError());
     return MG_OK;
 }
@@ -358,21 +366,58 @@ mg_status run_vcycle(mg_handle* h, const double* b, double* x, cudaStream_t s) {
 }
 
 // ---- GCR (Sec. 4.1; textbook generalised conjugate residual, right preconditioned) ----
-template <typename ApplyA, typename ApplyP>
+// Per iteration j of a restart cycle: z_j = P r (raw), w_j = A z_j with the inner products
+// <w_j, w_i>, <r, w_i>, <w_j, w_j>, <r, w_j> fused into the same pass (coefficients by
+// classical Gram-Schmidt), then one pass orthogonalises w_j in place and updates r with
+// <r, r>.  x is formed from the raw z_i once per cycle (or at the end).
+template <int JM>
+mg_status launch_gcr_sums(mg_handle* h, size_t n, const double* w, int j, cudaStream_t s) {
+    Prof pr(h, MG_K_GCR_DOTS, 0, 8.0 * n * (j + 2), s);
+    mg::k_gcr_sums<JM><<<h->red_grid, mg::RED_THREADS, 0, s>>>(n, w, h->W, h->glen, j, h->r, h->partials,
+                                                                h->tickets + TK_SUMS, h->gs);
+    CK(cudaGetLastError());
+    return MG_OK;
+}
+
+mg_status gcr_sums(mg_handle* h, size_t n, const double* w, int j, cudaStream_t s) {
+    if (j <= 4) return launch_gcr_sums<4>(h, n, w, j, s);
+    if (j <= 8) return launch_gcr_sums<8>(h, n, w, j, s);
+    return launch_gcr_sums<mg::MAXR>(h, n, w, j, s);
+}
+
+template <int JM>
+mg_status launch_apply_gcr(mg_handle* h, const double* z, double* w, int j, cudaStream_t s) {
+    const Lvl<double, double> L = View<double, double>::lvl(h, 0);
+    const double nc = (double)L.nlev * L.ncol;
+    Prof pr(h, MG_K_APPLY, 0, nc * 8.0 * (1 + 3 + 1 + 1 + j), s);
+    const int kc = APPLY_KCHUNK;
+    dim3 grid((L.ncol + mg::RED_THREADS - 1) / mg::RED_THREADS, (L.nlev + kc - 1) / kc);
+    mg::k_apply_gcr<JM><<<grid, mg::RED_THREADS, 0, s>>>(L, z, w, h->W, h->glen, j, h->r, kc, h->partials,
+                                                         h->tickets + TK_SUMS, h->gs);
+    CK(cudaGetLastError());
+    return MG_OK;
+}
+
+mg_status apply_gcr(mg_handle* h, const double* z, double* w, int j, cudaStream_t s) {
+    if (j <= 4) return launch_apply_gcr<4>(h, z, w, j, s);
+    if (j <= 8) return launch_apply_gcr<8>(h, z, w, j, s);
+    return launch_apply_gcr<mg::MAXR>(h, z, w, j, s);
+}
+
+template <typename ApplyAS, typename ApplyP>
 mg_status gcr(mg_handle* h, size_t n, const double* b, double* x, double tol, mg_solve_info* info,
-              cudaStream_t s, ApplyA applyA, ApplyP applyP) {
+              cudaStream_t s, ApplyAS applyAS, ApplyP applyP) {
     const int m = h->prm.gcr_restart;
     const int G = h->red_grid;
-    double* sc = h->sc;
     CK(cudaEventRecord(h->ev0, s));
     CK(cudaMemcpyAsync(h->r, b, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
     CK(cudaMemsetAsync(x, 0, n * sizeof(double), s));
     {
         Prof pr(h, MG_K_DOT, 0, 8.0 * n, s);
-        mg::k_dot<<<G, mg::RED_THREADS, 0, s>>>(n, b, b, h->partials, h->tickets + TK_DOT, sc + SC_BB);
+        mg::k_dot<<<G, mg::RED_THREADS, 0, s>>>(n, b, b, h->partials, h->tickets + TK_DOT, &h->gs->bb);
         CK(cudaGetLastError());
     }
-    CK(cudaMemcpyAsync(h->host_sc, sc + SC_BB, sizeof(double), cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(h->host_sc, &h->gs->bb, sizeof(double), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
     const double bb = h->host_sc[0];
     mg_status st = MG_OK;
@@ -382,32 +427,19 @@ mg_status gcr(mg_handle* h, size_t n, const double* b, double* x, double tol, mg
     else if (bb > 0.0) {
         rel = 1.0;
         st = MG_ERR_NOT_CONVERGED;
-        for (it = 0; it < h->prm.max_iter;) {
+        while (it < h->prm.max_iter) {
             const int j = it % m;
             double* z = h->Z + (size_t)j * h->glen;
             double* w = h->W + (size_t)j * h->glen;
             TRY(applyP(h->r, z));
-            TRY(applyA(z, w));
-            if (j > 0) {
-                Prof pr(h, MG_K_GCR_DOTS, 0, 8.0 * n * (j + 1), s);
-                mg::k_gcr_dots<<<G, mg::RED_THREADS, 0, s>>>(n, w, h->W, h->glen, j, h->partials,
-                                                              h->tickets + TK_DOTS, sc + SC_DOTS);
-                CK(cudaGetLastError());
-            }
+            TRY(applyAS(z, w, j));
             {
-                Prof pr(h, MG_K_GCR_ORTH, 0, 8.0 * n * (j > 0 ? 2 * j + 5 : 2), s);
-                mg::k_gcr_orth<<<G, mg::RED_THREADS, 0, s>>>(n, w, z, h->W, h->Z, h->glen, j, sc + SC_DOTS, sc + SC_WW,
-                                                          h->r, h->partials, h->tickets + TK_ORTH, sc + SC_TMP,
-                                                          sc + SC_ALPHA);
+                Prof pr(h, MG_K_GCR_ORTH, 0, 8.0 * n * (j > 0 ? j + 4 : 3), s);
+                mg::k_gcr_orth_update<<<G, mg::RED_THREADS, 0, s>>>(n, h->W, h->glen, j, h->r, h->partials,
+                                                                     h->tickets + TK_ORTH, h->gs);
                 CK(cudaGetLastError());
             }
-            {
-                Prof pr(h, MG_K_GCR_UPDATE, 0, 8.0 * n * 6, s);
-                mg::k_gcr_update<<<G, mg::RED_THREADS, 0, s>>>(n, x, h->r, z, w, sc + SC_ALPHA, h->partials,
-                                                            h->tickets + TK_UPD, sc + SC_RR);
-                CK(cudaGetLastError());
-            }
-            CK(cudaMemcpyAsync(h->host_sc, sc + SC_RR, sizeof(double), cudaMemcpyDeviceToHost, s));
+            CK(cudaMemcpyAsync(h->host_sc, &h->gs->rr, sizeof(double), cudaMemcpyDeviceToHost, s));
             CK(cudaStreamSynchronize(s));
             ++it;
             const double rr = h->host_sc[0];
@@ -416,7 +448,13 @@ mg_status gcr(mg_handle* h, size_t n, const double* b, double* x, double tol, mg
                 break;
             }
             rel = std::sqrt(rr / bb);
-            if (rel <= tol) {
+            const bool done = rel <= tol;
+            if (j == m - 1 || done || it == h->prm.max_iter) {
+                Prof pr(h, MG_K_GCR_UPDATE, 0, 8.0 * n * (j + 3), s);
+                mg::k_gcr_xupdate<<<G, mg::RED_THREADS, 0, s>>>(n, x, h->Z, h->glen, j, h->gs);
+                CK(cudaGetLastError());
+            }
+            if (done) {
                 st = MG_OK;
                 break;
             }
@@ -488,7 +526,7 @@ mg_status setup_impl(mg_handle* h, const mg_mesh* mesh, const mg_params* prm, co
     h->prm = *prm;
     CK(cudaGetDevice(&h->device));
     CK(cudaDeviceGetAttribute(&h->nsm, cudaDevAttrMultiProcessorCount, h->device));
-    h->red_grid = 2 * h->nsm;
+    h->red_grid = 8 * h->nsm;
     // host hierarchy
     std::vector<mg::HGeom> hg(L);
     for (int l = 0; l < L; ++l) {
@@ -621,11 +659,17 @@ mg_status setup_impl(mg_handle* h, const mg_mesh* mesh, const mg_params* prm, co
     TRY(dalloc(h, &h->Z, (size_t)prm->gcr_restart * h->glen));
     TRY(dalloc(h, &h->W, (size_t)prm->gcr_restart * h->glen));
     TRY(dalloc(h, &h->r, h->glen));
-    TRY(dalloc(h, &h->sc, SC_COUNT));
-    TRY(dalloc(h, &h->partials, (size_t)h->red_grid * mg::MAXR));
+    TRY(dalloc(h, &h->gs, 1));
+    {
+        const size_t apply_blocks = (size_t)((ncol0 + mg::RED_THREADS - 1) / mg::RED_THREADS) *
+                                    ((nlev + APPLY_KCHUNK - 1) / APPLY_KCHUNK);
+        const size_t blocks = apply_blocks > (size_t)h->red_grid ? apply_blocks : (size_t)h->red_grid;
+        h->npartials = blocks * (2 * mg::MAXR + 2);
+        TRY(dalloc(h, &h->partials, h->npartials));
+    }
     TRY(dalloc(h, &h->tickets, TK_COUNT));
     CK(cudaMemset(h->tickets, 0, TK_COUNT * sizeof(unsigned int)));
-    CK(cudaMemset(h->sc, 0, SC_COUNT * sizeof(double)));
+    CK(cudaMemset(h->gs, 0, sizeof(mg::GcrScal)));
     if (cudaMallocHost(&h->host_sc, 4 * sizeof(double)) != cudaSuccess) return MG_ERR_NOMEM;
     CK(cudaEventCreate(&h->ev0));
     CK(cudaEventCreate(&h->ev1));
@@ -719,8 +763,7 @@ mg_status pressure_solve(mg_handle* h, const double* b, double* x, double tol, m
     if (!h || !b || !x || b == x || !(tol >= 0.0)) return MG_ERR_ARG;
     DeviceGuard dg(h->device);
     cudaStream_t s = S(stream);
-    const Lvl<double, double> L0 = View<double, double>::lvl(h, 0);
-    auto A = [&](const double* v, double* y) { return launch_apply(h, 0, L0, v, y, s); };
+    auto A = [&](const double* z, double* w, int j) { return apply_gcr(h, z, w, j, s); };
     auto P = [&](const double* r, double* z) { return run_vcycle(h, r, z, s); };
     return gcr(h, cells(h, 0), b, x, tol, info, s, A, P);
 }
@@ -735,7 +778,10 @@ mg_status mixed_solve(mg_handle* h, const double* rhs_u, const double* rhs_p, do
     // GCR runs on concatenated [u; p] vectors held by the handle
     CK(cudaMemcpyAsync(h->mb, rhs_u, nu * sizeof(double), cudaMemcpyDeviceToDevice, s));
     CK(cudaMemcpyAsync(h->mb + nu, rhs_p, np * sizeof(double), cudaMemcpyDeviceToDevice, s));
-    auto A = [&](const double* v, double* y) { return mixed_apply_impl(h, v, v + nu, y, y + nu, s); };
+    auto A = [&](const double* v, double* y, int j) {
+        TRY(mixed_apply_impl(h, v, v + nu, y, y + nu, s));
+        return gcr_sums(h, n, y, j, s);
+    };
     auto P = [&](const double* r, double* z) { return schur_impl(h, r, r + nu, z, z + nu, s); };
     const mg_status st = gcr(h, n, h->mb, h->mx, tol, info, s, A, P);
     if (st == MG_OK || st == MG_ERR_NOT_CONVERGED || st == MG_ERR_BREAKDOWN) {
