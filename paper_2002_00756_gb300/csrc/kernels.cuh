@@ -112,23 +112,26 @@ __global__ void __launch_bounds__(256) k_apply(Lvl<T, C> L, const X* __restrict_
 // pass substitutes and writes x_out.  Optionally copies b into `bcopy` (entry of the
 // FP32 V-cycle, where b arrives in FP64).
 //
-// Latency hiding: the loads of level k + PF are issued before level k is computed, into a
-// register ring of PF levels (the loop over k is unrolled by PF so the ring is indexed
-// statically); the elimination recurrence then never waits on memory.
-template <typename T, typename X, bool PRO>
-struct SweepLv {
-    T xp;                   // own column, level k+1 (raw iterate)
-    T xn[4];                // E, W, N, S neighbours, level k (raw iterate)
-    T cp, cn[4];            // prolongation terms (PRO only)
-    T th[4];                // horizontal face coefficients
-    T tup;                  // vertical face above
-    T b;
+// Latency hiding: loads are issued ahead into register rings, indexed statically because
+// the loop over k is unrolled by the ring length: the streams met first in DRAM (own
+// column: x above, b, the E and N face coefficients, the face above) run DEEP levels
+// ahead; the loads that mostly hit in cache (W and S faces, the four neighbour iterates,
+// prolongation terms) run SHAL levels ahead.  The elimination recurrence then never waits
+// on memory.
+template <typename T>
+struct SweepDeep {
+    T xp, b, te, tn, tup;
+};
+template <typename T>
+struct SweepShal {
+    T xn[4], tw, ts, cp, cn[4];
 };
 
-template <typename T, typename C, int MODE, typename X, typename B, typename O, bool BCOPY, int PF>
+template <typename T, typename C, int MODE, typename X, typename B, typename O, bool BCOPY, int DEEP, int SHAL>
 __global__ void k_sweep(Lvl<T, C> L, const X* __restrict__ x, const T* __restrict__ xc,
                         int ncol_c, const B* __restrict__ b, T* __restrict__ bcopy,
                         O* __restrict__ xo, T omega) {
+    static_assert(DEEP % SHAL == 0, "ring lengths");
     constexpr bool PRO = (MODE == XM_PROLONG || MODE == XM_PROLONG0);
     constexpr bool RAW = (MODE == XM_PLAIN || MODE == XM_PROLONG);   // reads the fine iterate
     extern __shared__ unsigned char smem_raw[];
@@ -151,65 +154,76 @@ __global__ void k_sweep(Lvl<T, C> L, const X* __restrict__ x, const T* __restric
     }
     const T rA = __ldg(L.rA + c);
 
-    auto load = [&](int k, SweepLv<T, X, PRO>& d) {
+    auto load_deep = [&](int k, SweepDeep<T>& d) {
+        const size_t o = (size_t)k * ncol;
+        const C* th = L.Th + (size_t)k * nf;
+        if (RAW) d.xp = (k + 1 < nlev) ? ldx<T>(x + o + ncol + c) : T(0);
+        d.b = (T)__ldg(b + o + c);
+        d.te = ldc<T>(th + fo[0]);
+        d.tn = ldc<T>(th + fo[2]);
+        d.tup = ldc<T>(L.Tv + o + ncol + c);
+    };
+    auto load_shal = [&](int k, SweepShal<T>& d) {
         const size_t o = (size_t)k * ncol, oc = (size_t)k * ncol_c;
-        const bool up = k + 1 < nlev;
+        const C* th = L.Th + (size_t)k * nf;
         if (RAW) {
-            d.xp = up ? ldx<T>(x + o + ncol + c) : T(0);
 #pragma unroll
             for (int s = 0; s < 4; ++s) d.xn[s] = ldx<T>(x + o + nb[s]);
         }
         if (PRO) {
-            d.cp = up ? __ldg(xc + oc + ncol_c + pc) : T(0);
+            d.cp = (k + 1 < nlev) ? __ldg(xc + oc + ncol_c + pc) : T(0);
 #pragma unroll
             for (int s = 0; s < 4; ++s) d.cn[s] = __ldg(xc + oc + pn[s]);
         }
-        const C* th = L.Th + (size_t)k * nf;
-#pragma unroll
-        for (int s = 0; s < 4; ++s) d.th[s] = ldc<T>(th + fo[s]);
-        d.tup = ldc<T>(L.Tv + o + ncol + c);
-        d.b = (T)__ldg(b + o + c);
+        d.tw = ldc<T>(th + fo[1]);
+        d.ts = ldc<T>(th + fo[3]);
     };
 
-    SweepLv<T, X, PRO> ring[PF];
+    SweepDeep<T> dr[DEEP];
+    SweepShal<T> sr[SHAL];
 #pragma unroll
-    for (int j = 0; j < PF; ++j)
-        if (j < nlev) load(j, ring[j]);
+    for (int j = 0; j < DEEP; ++j)
+        if (j < nlev) load_deep(j, dr[j]);
+#pragma unroll
+    for (int j = 0; j < SHAL; ++j)
+        if (j < nlev) load_shal(j, sr[j]);
     T xm = T(0), x0 = T(0), tdn = T(0);
     if (RAW) x0 = ldx<T>(x + c);
     if (PRO) x0 += __ldg(xc + pc);
     T q = T(0), ip = T(0), y = T(0);
-    for (int k0 = 0; k0 < nlev; k0 += PF) {
+    for (int k0 = 0; k0 < nlev; k0 += DEEP) {
 #pragma unroll
-        for (int j = 0; j < PF; ++j) {
+        for (int j = 0; j < DEEP; ++j) {
             const int k = k0 + j;
             if (k < nlev) {
-                const SweepLv<T, X, PRO> d = ring[j];
-                if (k + PF < nlev) load(k + PF, ring[j]);
+                const SweepDeep<T> d = dr[j];
+                const SweepShal<T> e = sr[j % SHAL];
+                if (k + DEEP < nlev) load_deep(k + DEEP, dr[j]);
+                if (k + SHAL < nlev) load_shal(k + SHAL, sr[j % SHAL]);
                 T xp = T(0), xe[4] = {T(0), T(0), T(0), T(0)};
                 if (RAW) {
                     xp = d.xp;
 #pragma unroll
-                    for (int s = 0; s < 4; ++s) xe[s] = d.xn[s];
+                    for (int s = 0; s < 4; ++s) xe[s] = e.xn[s];
                 }
                 if (PRO) {
-                    xp += d.cp;
+                    xp += e.cp;
 #pragma unroll
-                    for (int s = 0; s < 4; ++s) xe[s] += d.cn[s];
+                    for (int s = 0; s < 4; ++s) xe[s] += e.cn[s];
                 }
                 const T rdz = __ldg(L.rdz + k);
                 if (BCOPY) bcopy[(size_t)k * ncol + c] = d.b;
                 T r = d.b;
                 if (MODE != XM_ZERO) {
-                    T hx = d.th[0] * (x0 - xe[0]);
-                    hx += d.th[1] * (x0 - xe[1]);
-                    hx += d.th[2] * (x0 - xe[2]);
-                    hx += d.th[3] * (x0 - xe[3]);
+                    T hx = d.te * (x0 - xe[0]);
+                    hx += e.tw * (x0 - xe[1]);
+                    hx += d.tn * (x0 - xe[2]);
+                    hx += e.ts * (x0 - xe[3]);
                     r -= x0 + (rA * hx + rdz * (d.tup * (x0 - xp) + tdn * (x0 - xm)));
                 }
                 const T aup = rdz * d.tup, adn = rdz * tdn;
                 const T m = adn * ip;
-                q = (T(1) + rA * ((d.th[0] + d.th[1]) + (d.th[2] + d.th[3]))) + m * q;
+                q = (T(1) + rA * ((d.te + e.tw) + (d.tn + e.ts))) + m * q;
                 const T p = q + aup;
                 y = r + m * y;
                 ip = T(1) / p;

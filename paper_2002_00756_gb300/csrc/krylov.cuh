@@ -98,34 +98,28 @@ __global__ void __launch_bounds__(RED_THREADS) k_dot(size_t n, const double* __r
 
 // GCR step coefficients for direction j (classical Gram-Schmidt, one pass):
 //   beta_i = <w, w_i> / <w_i, w_i>,  <w', w'> = <w, w> - sum_i beta_i <w, w_i>,
-//   <r, w'> = <r, w> - sum_i beta_i <r, w_i>,  alpha = <r, w'> / <w', w'>,
-// with sums = [<w, w_i> (JM), <r, w_i> (JM), <w, w>, <r, w>].
+//   alpha = <r, w'> / <w', w'> with <r, w'> = <r, w> (the GCR residual is orthogonal to
+//   all earlier directions w_i), from sums = [<w, w_i> (JM), <w, w>, <r, w>].
 template <int JM>
-__device__ void gcr_coeffs(int j, const double (&t)[2 * JM + 2], GcrScal* S) {
-    double ww = t[2 * JM], rw = t[2 * JM + 1];
+__device__ void gcr_coeffs(int j, const double (&t)[JM + 2], GcrScal* S) {
+    double ww = t[JM];
     for (int i = 0; i < j; ++i) {
         const double beta = t[i] / S->ww[i];
         S->beta[j * MAXR + i] = beta;
         ww -= beta * t[i];
-        rw -= beta * t[JM + i];
     }
-    S->alpha[j] = rw / ww;
+    S->alpha[j] = t[JM + 1] / ww;
 }
 
 // Accumulates the GCR sums of one element: w_e, r_e and the stored directions W_i[e].
 template <int JM>
-__device__ __forceinline__ void gcr_accumulate(double (&v)[2 * JM + 2], double we, double re,
+__device__ __forceinline__ void gcr_accumulate(double (&v)[JM + 2], double we, double re,
                                                const double* __restrict__ Wb, size_t ld, size_t e, int j) {
 #pragma unroll
-    for (int i = 0; i < JM; ++i) {
-        if (i < j) {
-            const double wi = __ldg(Wb + (size_t)i * ld + e);
-            v[i] += we * wi;
-            v[JM + i] += re * wi;
-        }
-    }
-    v[2 * JM] += we * we;
-    v[2 * JM + 1] += re * we;
+    for (int i = 0; i < JM; ++i)
+        if (i < j) v[i] += we * __ldg(Wb + (size_t)i * ld + e);
+    v[JM] += we * we;
+    v[JM + 1] += re * we;
 }
 
 // GCR sums for a new direction w (mixed system path, where w comes from other kernels).
@@ -134,12 +128,12 @@ __global__ void __launch_bounds__(RED_THREADS) k_gcr_sums(size_t n, const double
                                                           const double* __restrict__ Wb, size_t ld, int j,
                                                           const double* __restrict__ r, double* partials,
                                                           unsigned int* ticket, GcrScal* S) {
-    double v[2 * JM + 2], t[2 * JM + 2];
+    double v[JM + 2], t[JM + 2];
 #pragma unroll
-    for (int i = 0; i < 2 * JM + 2; ++i) v[i] = 0.0;
+    for (int i = 0; i < JM + 2; ++i) v[i] = 0.0;
     for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x)
         gcr_accumulate<JM>(v, __ldg(w + e), __ldg(r + e), Wb, ld, e, j);
-    if (grid_reduce<2 * JM + 2>(v, partials, ticket, t)) gcr_coeffs<JM>(j, t, S);
+    if (grid_reduce<JM + 2>(v, partials, ticket, t)) gcr_coeffs<JM>(j, t, S);
 }
 
 // w_j <- w_j - sum_i beta_i w_i (stored in place), r <- r - alpha_j w_j,
@@ -286,9 +280,9 @@ __global__ void __launch_bounds__(RED_THREADS) k_apply_gcr(Lvl<double, double> L
                                                            size_t ld, int j, const double* __restrict__ r,
                                                            int kchunk, double* partials, unsigned int* ticket,
                                                            GcrScal* S) {
-    double v[2 * JM + 2], t[2 * JM + 2];
+    double v[JM + 2], t[JM + 2];
 #pragma unroll
-    for (int i = 0; i < 2 * JM + 2; ++i) v[i] = 0.0;
+    for (int i = 0; i < JM + 2; ++i) v[i] = 0.0;
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
     if (c < L.ncol) {
         const size_t ncol = L.ncol, nf = 2 * ncol;
@@ -321,7 +315,7 @@ __global__ void __launch_bounds__(RED_THREADS) k_apply_gcr(Lvl<double, double> L
             tdn = tup;
         }
     }
-    if (grid_reduce<2 * JM + 2>(v, partials, ticket, t)) gcr_coeffs<JM>(j, t, S);
+    if (grid_reduce<JM + 2>(v, partials, ticket, t)) gcr_coeffs<JM>(j, t, S);
 }
 
 }  // namespace mg

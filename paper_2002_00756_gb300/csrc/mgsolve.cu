@@ -221,10 +221,11 @@ mg_status launch_apply(mg_handle* h, int lev, const Lvl<T, C>& L, const X* x, Y*
     return MG_OK;
 }
 
-// prefetch depth of the sweep's register ring (levels in flight per thread)
+// prefetch depths of the sweep's register rings (levels in flight per thread)
 template <typename T>
 struct SweepPF {
-    static constexpr int value = sizeof(T) == 8 ? 2 : 4;
+    static constexpr int deep = sizeof(T) == 8 ? 4 : 8;
+    static constexpr int shal = sizeof(T) == 8 ? 2 : 4;
 };
 
 template <typename T, typename C, int MODE, typename X, typename B, typename O, bool BCOPY>
@@ -243,11 +244,11 @@ mg_status launch_sweep(mg_handle* h, int lev, const Lvl<T, C>& L, const X* x, co
     if (bd > cap) bd = cap;
     const size_t smem = 2 * (size_t)L.nlev * bd * sizeof(T);
     if (smem > 48 * 1024)
-        CK(cudaFuncSetAttribute(mg::k_sweep<T, C, MODE, X, B, O, BCOPY, SweepPF<T>::value>,
+        CK(cudaFuncSetAttribute(mg::k_sweep<T, C, MODE, X, B, O, BCOPY, SweepPF<T>::deep, SweepPF<T>::shal>,
                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     const int grid = (L.ncol + bd - 1) / bd;
-    mg::k_sweep<T, C, MODE, X, B, O, BCOPY, SweepPF<T>::value><<<grid, bd, smem, s>>>(L, x, xc, ncol_c, b, bcopy,
-                                                                                     xo, (T)omega);
+    mg::k_sweep<T, C, MODE, X, B, O, BCOPY, SweepPF<T>::deep, SweepPF<T>::shal>
+        <<<grid, bd, smem, s>>>(L, x, xc, ncol_c, b, bcopy, xo, (T)omega);
     CK(cudaGetLastError());
     return MG_OK;
 }
@@ -372,7 +373,7 @@ mg_status run_vcycle(mg_handle* h, const double* b, double* x, cudaStream_t s) {
 // <r, r>.  x is formed from the raw z_i once per cycle (or at the end).
 template <int JM>
 mg_status launch_gcr_sums(mg_handle* h, size_t n, const double* w, int j, cudaStream_t s) {
-    Prof pr(h, MG_K_GCR_DOTS, 0, 8.0 * n * (j + 2), s);
+    Prof pr(h, MG_K_GCR_DOTS, 0, 8.0 * n * (j + 2), s);   // w, r, w_i
     mg::k_gcr_sums<JM><<<h->red_grid, mg::RED_THREADS, 0, s>>>(n, w, h->W, h->glen, j, h->r, h->partials,
                                                                 h->tickets + TK_SUMS, h->gs);
     CK(cudaGetLastError());
@@ -389,7 +390,7 @@ template <int JM>
 mg_status launch_apply_gcr(mg_handle* h, const double* z, double* w, int j, cudaStream_t s) {
     const Lvl<double, double> L = View<double, double>::lvl(h, 0);
     const double nc = (double)L.nlev * L.ncol;
-    Prof pr(h, MG_K_APPLY, 0, nc * 8.0 * (1 + 3 + 1 + 1 + j), s);
+    Prof pr(h, MG_K_APPLY, 0, nc * 8.0 * (1 + 3 + 1 + 1 + j), s);   // z, 3 coefficients, w, r, w_i
     const int kc = APPLY_KCHUNK;
     dim3 grid((L.ncol + mg::RED_THREADS - 1) / mg::RED_THREADS, (L.nlev + kc - 1) / kc);
     mg::k_apply_gcr<JM><<<grid, mg::RED_THREADS, 0, s>>>(L, z, w, h->W, h->glen, j, h->r, kc, h->partials,
@@ -654,8 +655,9 @@ mg_status setup_impl(mg_handle* h, const mg_mesh* mesh, const mg_params* prm, co
         TRY(dalloc(h, &h->mb, (size_t)h->nu + N0));
         TRY(dalloc(h, &h->mx, (size_t)h->nu + N0));
     }
-    // GCR workspace
-    h->glen = N0 + (size_t)h->nu;
+    // GCR workspace; the slot stride is padded off a multiple of large powers of two so
+    // the directions streamed side by side do not share their low address bits
+    h->glen = (N0 + (size_t)h->nu + 63) / 64 * 64 + 96;
     TRY(dalloc(h, &h->Z, (size_t)prm->gcr_restart * h->glen));
     TRY(dalloc(h, &h->W, (size_t)prm->gcr_restart * h->glen));
     TRY(dalloc(h, &h->r, h->glen));
