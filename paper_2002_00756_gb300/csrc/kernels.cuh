@@ -105,26 +105,34 @@ __global__ void __launch_bounds__(256) k_apply(Lvl<T, C> L, const X* __restrict_
 }
 
 // ---------------------------------------------------------------------------------------
-// One block-Jacobi sweep (Eq. jacobi): x_out = x + omega Hz^{-1} (b - H x), per column:
-// forward pass computes the residual and eliminates with pivots p_k = q_k + a_up_k,
-// q_k = s_k + (a_dn_k / p_{k-1}) q_{k-1} (s_k = 1 + horizontal coefficients, so no
-// subtraction), stashing y_k / p_k and a_up_k / p_k in shared memory; the backward
-// pass substitutes and writes x_out.  Optionally copies b into `bcopy` (entry of the
-// FP32 V-cycle, where b arrives in FP64).
+// One block-Jacobi sweep (Eq. jacobi): x_out = x + omega Hz^{-1} (b - H x).
 //
-// Latency hiding: loads are issued ahead into register rings, indexed statically because
-// the loop over k is unrolled by the ring length: the streams met first in DRAM (own
-// column: x above, b, the E and N face coefficients, the face above) run DEEP levels
-// ahead; the loads that mostly hit in cache (W and S faces, the four neighbour iterates,
-// prolongation terms) run SHAL levels ahead.  The elimination recurrence then never waits
-// on memory.
+// Two threads per column solve its tridiagonal system from both ends (a twisted
+// factorisation): lanes 0-15 of a warp take the lower half of 16 columns and eliminate
+// upwards from the surface, lanes 16-31 take the upper half of the same columns and
+// eliminate downwards from the lid.  With the coupling to the already-eliminated
+// neighbour a_prev and to the next one a_next, every step is
+//     m = a_prev / p_prev,  q = s + m q_prev,  p = q + a_next,  y = r + m y_prev
+// (s = 1 + horizontal coefficients: pivots are sums of positive terms).  The two halves
+// meet at rows h-1 and h; their 2x2 system
+//     [p_A  -a_A] [x_A]   [y_A]
+//     [-a_B  p_B] [x_B] = [y_B],   det = q_A p_B + a_A q_B  (no cancellation)
+// is solved by both lanes after a shuffle, then each half back-substitutes towards its
+// end.  Per step the thread stashes y/p and a_next/p in shared memory.  Compared with one
+// thread per column this doubles the resident warps for the same stash and halves the
+// serial recurrence.
+//
+// Latency hiding: loads run ahead of use in register rings indexed statically (the step
+// loop is unrolled by the ring length): the streams first met in DRAM (the next iterate of
+// the own column, b, the E and N faces, the vertical face ahead) DEEP steps ahead; loads
+// that mostly hit in cache (W and S faces, neighbour iterates, prolongation) SHAL ahead.
 template <typename T>
 struct SweepDeep {
-    T xp, b, te, tn, tup;
+    T xn, b, te, tn, tv;
 };
 template <typename T>
 struct SweepShal {
-    T xn[4], tw, ts, cp, cn[4];
+    T xh[4], tw, ts, cn, ch[4];
 };
 
 template <typename T, typename C, int MODE, typename X, typename B, typename O, bool BCOPY, int DEEP, int SHAL>
@@ -135,11 +143,18 @@ __global__ void k_sweep(Lvl<T, C> L, const X* __restrict__ x, const T* __restric
     constexpr bool PRO = (MODE == XM_PROLONG || MODE == XM_PROLONG0);
     constexpr bool RAW = (MODE == XM_PLAIN || MODE == XM_PROLONG);   // reads the fine iterate
     extern __shared__ unsigned char smem_raw[];
+    const int nlev = L.nlev, hsteps = (nlev + 1) >> 1;
     T* sc = reinterpret_cast<T*>(smem_raw);
-    T* se = sc + (size_t)L.nlev * blockDim.x;
-    const int c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= L.ncol) return;
-    const int tid = threadIdx.x, bd = blockDim.x, nlev = L.nlev;
+    T* se = sc + (size_t)hsteps * blockDim.x;
+    const int lane = threadIdx.x & 31;
+    const bool upper = lane >= 16;
+    const int c_raw = blockIdx.x * (blockDim.x >> 1) + (threadIdx.x >> 5) * 16 + (lane & 15);
+    const bool active = c_raw < L.ncol;
+    const int c = active ? c_raw : L.ncol - 1;
+    const int tid = threadIdx.x, bd = blockDim.x;
+    const int nsteps = upper ? nlev - hsteps : hsteps;
+    const int dir = upper ? -1 : 1;
+    const int kfirst = upper ? nlev - 1 : 0;
     const size_t ncol = L.ncol, nf = 2 * ncol;
     int nb[4], fo[4], pn[4] = {0, 0, 0, 0}, pc = 0;
 #pragma unroll
@@ -154,26 +169,31 @@ __global__ void k_sweep(Lvl<T, C> L, const X* __restrict__ x, const T* __restric
     }
     const T rA = __ldg(L.rA + c);
 
-    auto load_deep = [&](int k, SweepDeep<T>& d) {
+    // step i works on level kfirst + dir * i; the vertical face towards the next level in
+    // the walk is Tv[k+1] going up and Tv[k] going down
+    auto load_deep = [&](int i, SweepDeep<T>& d) {
+        const int k = kfirst + dir * i;
+        const int kn = k + dir;
         const size_t o = (size_t)k * ncol;
         const C* th = L.Th + (size_t)k * nf;
-        if (RAW) d.xp = (k + 1 < nlev) ? ldx<T>(x + o + ncol + c) : T(0);
+        if (RAW) d.xn = (kn >= 0 && kn < nlev) ? ldx<T>(x + (size_t)kn * ncol + c) : T(0);
+        if (PRO) d.xn += (kn >= 0 && kn < nlev) ? __ldg(xc + (size_t)kn * ncol_c + pc) : T(0);
         d.b = (T)__ldg(b + o + c);
         d.te = ldc<T>(th + fo[0]);
         d.tn = ldc<T>(th + fo[2]);
-        d.tup = ldc<T>(L.Tv + o + ncol + c);
+        d.tv = ldc<T>(L.Tv + (size_t)(upper ? k : k + 1) * ncol + c);
     };
-    auto load_shal = [&](int k, SweepShal<T>& d) {
+    auto load_shal = [&](int i, SweepShal<T>& d) {
+        const int k = kfirst + dir * i;
         const size_t o = (size_t)k * ncol, oc = (size_t)k * ncol_c;
         const C* th = L.Th + (size_t)k * nf;
         if (RAW) {
 #pragma unroll
-            for (int s = 0; s < 4; ++s) d.xn[s] = ldx<T>(x + o + nb[s]);
+            for (int s = 0; s < 4; ++s) d.xh[s] = ldx<T>(x + o + nb[s]);
         }
         if (PRO) {
-            d.cp = (k + 1 < nlev) ? __ldg(xc + oc + ncol_c + pc) : T(0);
 #pragma unroll
-            for (int s = 0; s < 4; ++s) d.cn[s] = __ldg(xc + oc + pn[s]);
+            for (int s = 0; s < 4; ++s) d.ch[s] = __ldg(xc + oc + pn[s]);
         }
         d.tw = ldc<T>(th + fo[1]);
         d.ts = ldc<T>(th + fo[3]);
@@ -183,62 +203,79 @@ __global__ void k_sweep(Lvl<T, C> L, const X* __restrict__ x, const T* __restric
     SweepShal<T> sr[SHAL];
 #pragma unroll
     for (int j = 0; j < DEEP; ++j)
-        if (j < nlev) load_deep(j, dr[j]);
+        if (j < nsteps) load_deep(j, dr[j]);
 #pragma unroll
     for (int j = 0; j < SHAL; ++j)
-        if (j < nlev) load_shal(j, sr[j]);
-    T xm = T(0), x0 = T(0), tdn = T(0);
-    if (RAW) x0 = ldx<T>(x + c);
-    if (PRO) x0 += __ldg(xc + pc);
-    T q = T(0), ip = T(0), y = T(0);
-    for (int k0 = 0; k0 < nlev; k0 += DEEP) {
+        if (j < nsteps) load_shal(j, sr[j]);
+    T xprev = T(0), x0 = T(0), tprev = T(0);
+    if (RAW) x0 = ldx<T>(x + (size_t)kfirst * ncol + c);
+    if (PRO) x0 += __ldg(xc + (size_t)kfirst * ncol_c + pc);
+    T q = T(0), ip = T(0), y = T(0), anext = T(0);
+    for (int i0 = 0; i0 < hsteps; i0 += DEEP) {
 #pragma unroll
         for (int j = 0; j < DEEP; ++j) {
-            const int k = k0 + j;
-            if (k < nlev) {
+            const int i = i0 + j;
+            if (i < nsteps) {
                 const SweepDeep<T> d = dr[j];
                 const SweepShal<T> e = sr[j % SHAL];
-                if (k + DEEP < nlev) load_deep(k + DEEP, dr[j]);
-                if (k + SHAL < nlev) load_shal(k + SHAL, sr[j % SHAL]);
-                T xp = T(0), xe[4] = {T(0), T(0), T(0), T(0)};
+                if (i + DEEP < nsteps) load_deep(i + DEEP, dr[j]);
+                if (i + SHAL < nsteps) load_shal(i + SHAL, sr[j % SHAL]);
+                const int k = kfirst + dir * i;
+                T xh[4] = {T(0), T(0), T(0), T(0)};
                 if (RAW) {
-                    xp = d.xp;
 #pragma unroll
-                    for (int s = 0; s < 4; ++s) xe[s] = e.xn[s];
+                    for (int s = 0; s < 4; ++s) xh[s] = e.xh[s];
                 }
                 if (PRO) {
-                    xp += e.cp;
 #pragma unroll
-                    for (int s = 0; s < 4; ++s) xe[s] += e.cn[s];
+                    for (int s = 0; s < 4; ++s) xh[s] += e.ch[s];
                 }
                 const T rdz = __ldg(L.rdz + k);
                 if (BCOPY) bcopy[(size_t)k * ncol + c] = d.b;
                 T r = d.b;
                 if (MODE != XM_ZERO) {
-                    T hx = d.te * (x0 - xe[0]);
-                    hx += e.tw * (x0 - xe[1]);
-                    hx += d.tn * (x0 - xe[2]);
-                    hx += e.ts * (x0 - xe[3]);
-                    r -= x0 + (rA * hx + rdz * (d.tup * (x0 - xp) + tdn * (x0 - xm)));
+                    T hx = d.te * (x0 - xh[0]);
+                    hx += e.tw * (x0 - xh[1]);
+                    hx += d.tn * (x0 - xh[2]);
+                    hx += e.ts * (x0 - xh[3]);
+                    r -= x0 + (rA * hx + rdz * (d.tv * (x0 - d.xn) + tprev * (x0 - xprev)));
                 }
-                const T aup = rdz * d.tup, adn = rdz * tdn;
-                const T m = adn * ip;
+                anext = rdz * d.tv;
+                const T m = (rdz * tprev) * ip;
                 q = (T(1) + rA * ((d.te + e.tw) + (d.tn + e.ts))) + m * q;
-                const T p = q + aup;
+                const T p = q + anext;
                 y = r + m * y;
                 ip = T(1) / p;
-                sc[(size_t)k * bd + tid] = y * ip;
-                se[(size_t)k * bd + tid] = aup * ip;
-                xm = x0;
-                x0 = xp;
-                tdn = d.tup;
+                sc[(size_t)i * bd + tid] = y * ip;
+                se[(size_t)i * bd + tid] = anext * ip;
+                xprev = x0;
+                x0 = d.xn;
+                tprev = d.tv;
             }
         }
     }
-    T dlt = T(0);
+    // interface rows h-1 (lower half) and h (upper half)
+    const T qo = __shfl_xor_sync(0xffffffffu, q, 16);
+    const T yo = __shfl_xor_sync(0xffffffffu, y, 16);
+    const T ao = __shfl_xor_sync(0xffffffffu, anext, 16);
+    T dlt;
+    if (nlev - hsteps == 0) {
+        dlt = y * ip;   // single level: nothing above, anext = 0
+    } else {
+        const T po = qo + ao, pm = q + anext;
+        dlt = (y * po + anext * yo) / (q * po + anext * qo);
+        (void)pm;
+    }
+    if (!active || nsteps == 0) return;
+    {
+        const int k = kfirst + dir * (nsteps - 1);
+        const size_t o = (size_t)k * ncol, oc = (size_t)k * ncol_c;
+        xo[o + c] = (O)(xval<MODE, T>(x, xc, o, oc, c, pc) + omega * dlt);
+    }
 #pragma unroll 4
-    for (int k = nlev - 1; k >= 0; --k) {
-        dlt = sc[(size_t)k * bd + tid] + se[(size_t)k * bd + tid] * dlt;
+    for (int i = nsteps - 2; i >= 0; --i) {
+        dlt = sc[(size_t)i * bd + tid] + se[(size_t)i * bd + tid] * dlt;
+        const int k = kfirst + dir * i;
         const size_t o = (size_t)k * ncol, oc = (size_t)k * ncol_c;
         xo[o + c] = (O)(xval<MODE, T>(x, xc, o, oc, c, pc) + omega * dlt);
     }
@@ -246,15 +283,18 @@ __global__ void k_sweep(Lvl<T, C> L, const X* __restrict__ x, const T* __restric
 
 // ---------------------------------------------------------------------------------------
 // Residual and restriction (Algorithm 1): bc[k][C] = sum_q w[q][C] (b - H x)[k][child_q],
-// w = area_child / area_C; one thread per coarse column.
+// w = area_child / area_C; one thread per coarse column and chunk of kchunk levels (there is
+// no vertical recurrence, so short chunks give many independent threads).
 template <typename T, typename C, bool XZERO, typename X, typename B, typename O>
 __global__ void __launch_bounds__(128) k_resid_restrict(Lvl<T, C> L, const X* __restrict__ x,
                                                          const B* __restrict__ b,
                                                          const T* __restrict__ w,
-                                                         O* __restrict__ bc, int ncol_c) {
+                                                         O* __restrict__ bc, int ncol_c, int kchunk) {
     const int Cc = blockIdx.x * blockDim.x + threadIdx.x;
     if (Cc >= ncol_c) return;
     const size_t ncol = L.ncol, nf = 2 * ncol;
+    const int k0 = blockIdx.y * kchunk;
+    const int k1 = min(L.nlev, k0 + kchunk);
     int ch[4], nb[4][4], fo[4][4];
     T rA[4], wq[4], xm[4], x0[4], tdn[4];
 #pragma unroll
@@ -267,11 +307,11 @@ __global__ void __launch_bounds__(128) k_resid_restrict(Lvl<T, C> L, const X* __
         }
         rA[q] = __ldg(L.rA + ch[q]);
         wq[q] = __ldg(w + (size_t)q * ncol_c + Cc);
-        xm[q] = T(0);
-        x0[q] = XZERO ? T(0) : ldx<T>(x + ch[q]);
-        tdn[q] = T(0);
+        xm[q] = (XZERO || k0 == 0) ? T(0) : ldx<T>(x + (size_t)(k0 - 1) * ncol + ch[q]);
+        x0[q] = XZERO ? T(0) : ldx<T>(x + (size_t)k0 * ncol + ch[q]);
+        tdn[q] = ldc<T>(L.Tv + (size_t)k0 * ncol + ch[q]);
     }
-    for (int k = 0; k < L.nlev; ++k) {
+    for (int k = k0; k < k1; ++k) {
         const size_t o = (size_t)k * ncol;
         const C* th = L.Th + (size_t)k * nf;
         const T rdz = __ldg(L.rdz + k);

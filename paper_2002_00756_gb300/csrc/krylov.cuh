@@ -96,94 +96,97 @@ __global__ void __launch_bounds__(RED_THREADS) k_dot(size_t n, const double* __r
     if (grid_reduce<1>(v, partials, ticket, t)) *out = t[0];
 }
 
-// GCR step coefficients for direction j (classical Gram-Schmidt, one pass):
+// GCR step coefficients for direction J (classical Gram-Schmidt, one pass):
 //   beta_i = <w, w_i> / <w_i, w_i>,  <w', w'> = <w, w> - sum_i beta_i <w, w_i>,
 //   alpha = <r, w'> / <w', w'> with <r, w'> = <r, w> (the GCR residual is orthogonal to
-//   all earlier directions w_i), from sums = [<w, w_i> (JM), <w, w>, <r, w>].
-template <int JM>
-__device__ void gcr_coeffs(int j, const double (&t)[JM + 2], GcrScal* S) {
-    double ww = t[JM];
-    for (int i = 0; i < j; ++i) {
+//   all earlier directions w_i), from sums = [<w, w_i> (J), <w, w>, <r, w>].
+// Every kernel below is instantiated for the exact number J of stored directions, so no
+// FP64 instruction is spent on absent directions (FP64 issue rate bounds these kernels).
+template <int J>
+__device__ void gcr_coeffs(const double (&t)[J + 2], GcrScal* S) {
+    double ww = t[J];
+#pragma unroll
+    for (int i = 0; i < J; ++i) {
         const double beta = t[i] / S->ww[i];
-        S->beta[j * MAXR + i] = beta;
+        S->beta[J * MAXR + i] = beta;
         ww -= beta * t[i];
     }
-    S->alpha[j] = t[JM + 1] / ww;
+    S->alpha[J] = t[J + 1] / ww;
 }
 
-// Accumulates the GCR sums of one element: w_e, r_e and the stored directions W_i[e].
-template <int JM>
-__device__ __forceinline__ void gcr_accumulate(double (&v)[JM + 2], double we, double re,
-                                               const double* __restrict__ Wb, size_t ld, size_t e, int j) {
+template <int J>
+__device__ __forceinline__ void gcr_accumulate(double (&v)[J + 2], double we, double re,
+                                               const double* __restrict__ Wb, size_t ld, size_t e) {
 #pragma unroll
-    for (int i = 0; i < JM; ++i)
-        if (i < j) v[i] += we * __ldg(Wb + (size_t)i * ld + e);
-    v[JM] += we * we;
-    v[JM + 1] += re * we;
+    for (int i = 0; i < J; ++i) v[i] += we * __ldg(Wb + (size_t)i * ld + e);
+    v[J] += we * we;
+    v[J + 1] += re * we;
 }
 
 // GCR sums for a new direction w (mixed system path, where w comes from other kernels).
-template <int JM>
+template <int J>
 __global__ void __launch_bounds__(RED_THREADS) k_gcr_sums(size_t n, const double* __restrict__ w,
-                                                          const double* __restrict__ Wb, size_t ld, int j,
+                                                          const double* __restrict__ Wb, size_t ld,
                                                           const double* __restrict__ r, double* partials,
                                                           unsigned int* ticket, GcrScal* S) {
-    double v[JM + 2], t[JM + 2];
+    double v[J + 2], t[J + 2];
 #pragma unroll
-    for (int i = 0; i < JM + 2; ++i) v[i] = 0.0;
+    for (int i = 0; i < J + 2; ++i) v[i] = 0.0;
     for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x)
-        gcr_accumulate<JM>(v, __ldg(w + e), __ldg(r + e), Wb, ld, e, j);
-    if (grid_reduce<JM + 2>(v, partials, ticket, t)) gcr_coeffs<JM>(j, t, S);
+        gcr_accumulate<J>(v, __ldg(w + e), __ldg(r + e), Wb, ld, e);
+    if (grid_reduce<J + 2>(v, partials, ticket, t)) gcr_coeffs<J>(t, S);
 }
 
-// w_j <- w_j - sum_i beta_i w_i (stored in place), r <- r - alpha_j w_j,
-// then <w_j, w_j> -> ww[j] and <r, r> -> rr.
+// w_J <- w_J - sum_i beta_i w_i (stored in place), r <- r - alpha_J w_J,
+// then <w_J, w_J> -> ww[J] and <r, r> -> rr.
+template <int J>
 __global__ void __launch_bounds__(RED_THREADS) k_gcr_orth_update(size_t n, double* __restrict__ Wb, size_t ld,
-                                                                 int j, double* __restrict__ r,
-                                                                 double* partials, unsigned int* ticket,
-                                                                 GcrScal* S) {
-    double beta[MAXR];
+                                                                 double* __restrict__ r, double* partials,
+                                                                 unsigned int* ticket, GcrScal* S) {
+    double beta[J > 0 ? J : 1];
 #pragma unroll
-    for (int i = 0; i < MAXR; ++i) beta[i] = (i < j) ? S->beta[j * MAXR + i] : 0.0;
-    const double a = S->alpha[j];
-    double* w = Wb + (size_t)j * ld;
+    for (int i = 0; i < J; ++i) beta[i] = S->beta[J * MAXR + i];
+    const double a = S->alpha[J];
+    double* w = Wb + (size_t)J * ld;
     double v[2] = {0.0, 0.0}, t[2];
     for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
         double we = w[e];
 #pragma unroll
-        for (int i = 0; i < MAXR; ++i)
-            if (i < j) we -= beta[i] * __ldg(Wb + (size_t)i * ld + e);
-        if (j > 0) w[e] = we;
+        for (int i = 0; i < J; ++i) we -= beta[i] * __ldg(Wb + (size_t)i * ld + e);
+        if (J > 0) w[e] = we;
         const double re = r[e] - a * we;
         r[e] = re;
         v[0] += we * we;
         v[1] += re * re;
     }
     if (grid_reduce<2>(v, partials, ticket, t)) {
-        S->ww[j] = t[0];
+        S->ww[J] = t[0];
         S->rr = t[1];
     }
 }
 
-// x += sum_{i <= jl} gamma_i z_i with the raw (not orthogonalised) directions z_i:
+// x += sum_{i <= JL} gamma_i z_i with the raw (not orthogonalised) directions z_i:
 // x = sum_i alpha_i zhat_i, zhat_i = z_i - sum_{m<i} beta_im zhat_m, unrolled from the top.
-__global__ void k_gcr_xupdate(size_t n, double* __restrict__ x, const double* __restrict__ Zb, size_t ld, int jl,
+template <int JL>
+__global__ void k_gcr_xupdate(size_t n, double* __restrict__ x, const double* __restrict__ Zb, size_t ld,
                               const GcrScal* __restrict__ S) {
-    __shared__ double g[MAXR];
+    __shared__ double g[JL + 1];
     if (threadIdx.x == 0) {
-        double a[MAXR];
-        for (int i = 0; i <= jl; ++i) a[i] = S->alpha[i];
-        for (int i = jl; i >= 0; --i) {
+        double a[JL + 1];
+        for (int i = 0; i <= JL; ++i) a[i] = S->alpha[i];
+        for (int i = JL; i >= 0; --i) {
             g[i] = a[i];
             for (int m = 0; m < i; ++m) a[m] -= a[i] * S->beta[i * MAXR + m];
         }
     }
     __syncthreads();
+    double gr[JL + 1];
+#pragma unroll
+    for (int i = 0; i <= JL; ++i) gr[i] = g[i];
     for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
         double xe = x[e];
 #pragma unroll
-        for (int i = 0; i < MAXR; ++i)
-            if (i <= jl) xe += g[i] * __ldg(Zb + (size_t)i * ld + e);
+        for (int i = 0; i <= JL; ++i) xe += gr[i] * __ldg(Zb + (size_t)i * ld + e);
         x[e] = xe;
     }
 }
@@ -273,16 +276,15 @@ __global__ void k_mx_cells(MixedDev M, const double* __restrict__ uh, const doub
 }
 
 // Pressure-system GCR pass 1: w = H z (FP64, Eq. helmholtz_operator) for the levels
-// [k0, k0 + kchunk) of one column per thread, fused with the GCR sums of the new direction.
-template <int JM>
+// [k0, k0 + kchunk) of one column per thread, fused with the GCR sums of the new direction J.
+template <int J>
 __global__ void __launch_bounds__(RED_THREADS) k_apply_gcr(Lvl<double, double> L, const double* __restrict__ z,
                                                            double* __restrict__ w, const double* __restrict__ Wb,
-                                                           size_t ld, int j, const double* __restrict__ r,
-                                                           int kchunk, double* partials, unsigned int* ticket,
-                                                           GcrScal* S) {
-    double v[JM + 2], t[JM + 2];
+                                                           size_t ld, const double* __restrict__ r, int kchunk,
+                                                           double* partials, unsigned int* ticket, GcrScal* S) {
+    double v[J + 2], t[J + 2];
 #pragma unroll
-    for (int i = 0; i < JM + 2; ++i) v[i] = 0.0;
+    for (int i = 0; i < J + 2; ++i) v[i] = 0.0;
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
     if (c < L.ncol) {
         const size_t ncol = L.ncol, nf = 2 * ncol;
@@ -298,6 +300,7 @@ __global__ void __launch_bounds__(RED_THREADS) k_apply_gcr(Lvl<double, double> L
         double xm = k0 > 0 ? __ldg(z + (size_t)(k0 - 1) * ncol + c) : 0.0;
         double x0 = __ldg(z + (size_t)k0 * ncol + c);
         double tdn = __ldg(L.Tv + (size_t)k0 * ncol + c);
+#pragma unroll 2
         for (int k = k0; k < k1; ++k) {
             const size_t o = (size_t)k * ncol;
             const double xp = (k + 1 < L.nlev) ? __ldg(z + o + ncol + c) : 0.0;
@@ -309,13 +312,13 @@ __global__ void __launch_bounds__(RED_THREADS) k_apply_gcr(Lvl<double, double> L
             h += __ldg(th + fo[3]) * (x0 - __ldg(z + o + nb[3]));
             const double we = x0 + (rA * h + __ldg(L.rdz + k) * (tup * (x0 - xp) + tdn * (x0 - xm)));
             w[o + c] = we;
-            gcr_accumulate<JM>(v, we, __ldg(r + o + c), Wb, ld, o + c, j);
+            gcr_accumulate<J>(v, we, __ldg(r + o + c), Wb, ld, o + c);
             xm = x0;
             x0 = xp;
             tdn = tup;
         }
     }
-    if (grid_reduce<JM + 2>(v, partials, ticket, t)) gcr_coeffs<JM>(j, t, S);
+    if (grid_reduce<J + 2>(v, partials, ticket, t)) gcr_coeffs<J>(t, S);
 }
 
 }  // namespace mg

@@ -9,6 +9,7 @@
 #include <cstring>
 #include <new>
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "../../include/mgsolve.h"
@@ -237,16 +238,19 @@ mg_status launch_sweep(mg_handle* h, int lev, const Lvl<T, C>& L, const X* x, co
     if (MODE == mg::XM_PROLONG || MODE == mg::XM_PROLONG0) per += 0.25 * sizeof(T);
     if (BCOPY) per += sizeof(T);
     Prof pr(h, MG_K_SWEEP, lev, nc * per, s);
-    // the column stash (2 values per level per thread) must fit the shared-memory budget
-    int bd = sweep_block(L.ncol);
-    const int cap = (int)(SWEEP_SMEM_MAX / (2 * (size_t)L.nlev * sizeof(T))) / 32 * 32;
+    // two threads per column; the stash (2 values per step of half a column per thread)
+    // must fit the shared-memory budget
+    const int hsteps = (L.nlev + 1) / 2;
+    int bd = sweep_block(2 * L.ncol);
+    const int cap = (int)(SWEEP_SMEM_MAX / (2 * (size_t)hsteps * sizeof(T))) / 32 * 32;
     if (cap < 32) return MG_ERR_UNSUPPORTED;
     if (bd > cap) bd = cap;
-    const size_t smem = 2 * (size_t)L.nlev * bd * sizeof(T);
+    const size_t smem = 2 * (size_t)hsteps * bd * sizeof(T);
     if (smem > 48 * 1024)
         CK(cudaFuncSetAttribute(mg::k_sweep<T, C, MODE, X, B, O, BCOPY, SweepPF<T>::deep, SweepPF<T>::shal>,
                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    const int grid = (L.ncol + bd - 1) / bd;
+    const int cols = bd / 2;
+    const int grid = (L.ncol + cols - 1) / cols;
     mg::k_sweep<T, C, MODE, X, B, O, BCOPY, SweepPF<T>::deep, SweepPF<T>::shal>
         <<<grid, bd, smem, s>>>(L, x, xc, ncol_c, b, bcopy, xo, (T)omega);
     CK(cudaGetLastError());
@@ -260,7 +264,9 @@ mg_status launch_restrict(mg_handle* h, int lev, const Lvl<T, C>& L, const X* x,
     Prof pr(h, MG_K_RESTRICT, lev, nc * (sizeof(B) + 3 * sizeof(C) + (XZERO ? 0 : sizeof(X)) + 0.25 * sizeof(O) +
                                           sizeof(T) / (double)L.nlev), s);
     const int bd = ncol_c >= 128 * 300 ? 128 : (ncol_c >= 64 * 300 ? 64 : 32);
-    mg::k_resid_restrict<T, C, XZERO, X, B, O><<<(ncol_c + bd - 1) / bd, bd, 0, s>>>(L, x, b, w, bc, ncol_c);
+    const int kc = APPLY_KCHUNK;
+    const dim3 grid((ncol_c + bd - 1) / bd, (L.nlev + kc - 1) / kc);
+    mg::k_resid_restrict<T, C, XZERO, X, B, O><<<grid, bd, 0, s>>>(L, x, b, w, bc, ncol_c, kc);
     CK(cudaGetLastError());
     return MG_OK;
 }
@@ -371,38 +377,75 @@ mg_status run_vcycle(mg_handle* h, const double* b, double* x, cudaStream_t s) {
 // <w_j, w_i>, <r, w_i>, <w_j, w_j>, <r, w_j> fused into the same pass (coefficients by
 // classical Gram-Schmidt), then one pass orthogonalises w_j in place and updates r with
 // <r, r>.  x is formed from the raw z_i once per cycle (or at the end).
-template <int JM>
-mg_status launch_gcr_sums(mg_handle* h, size_t n, const double* w, int j, cudaStream_t s) {
-    Prof pr(h, MG_K_GCR_DOTS, 0, 8.0 * n * (j + 2), s);   // w, r, w_i
-    mg::k_gcr_sums<JM><<<h->red_grid, mg::RED_THREADS, 0, s>>>(n, w, h->W, h->glen, j, h->r, h->partials,
-                                                                h->tickets + TK_SUMS, h->gs);
-    CK(cudaGetLastError());
-    return MG_OK;
+// Run-time direction count j -> kernel instantiated for exactly j directions.
+template <template <int> class K, typename... A>
+mg_status dispatch_j(int j, A&&... a) {
+    switch (j) {
+#define MG_J(n) \
+    case n: return K<n>::run(std::forward<A>(a)...);
+        MG_J(0) MG_J(1) MG_J(2) MG_J(3) MG_J(4) MG_J(5) MG_J(6) MG_J(7)
+        MG_J(8) MG_J(9) MG_J(10) MG_J(11) MG_J(12) MG_J(13) MG_J(14) MG_J(15)
+#undef MG_J
+        default: return MG_ERR_ARG;
+    }
 }
+
+// column-chunk of the fused apply: long enough to amortise the per-thread reduction
+constexpr int GCR_APPLY_KCHUNK = 24;
+
+template <int J>
+struct RunSums {
+    static mg_status run(mg_handle* h, size_t n, const double* w, cudaStream_t s) {
+        Prof pr(h, MG_K_GCR_DOTS, 0, 8.0 * n * (J + 2), s);   // w, r, w_i
+        mg::k_gcr_sums<J><<<h->red_grid, mg::RED_THREADS, 0, s>>>(n, w, h->W, h->glen, h->r, h->partials,
+                                                                   h->tickets + TK_SUMS, h->gs);
+        CK(cudaGetLastError());
+        return MG_OK;
+    }
+};
+
+template <int J>
+struct RunApplyGcr {
+    static mg_status run(mg_handle* h, const double* z, double* w, cudaStream_t s) {
+        const Lvl<double, double> L = View<double, double>::lvl(h, 0);
+        const double nc = (double)L.nlev * L.ncol;
+        Prof pr(h, MG_K_APPLY, 0, nc * 8.0 * (1 + 3 + 1 + 1 + J), s);   // z, 3 coefficients, w, r, w_i
+        const int kc = GCR_APPLY_KCHUNK;
+        dim3 grid((L.ncol + mg::RED_THREADS - 1) / mg::RED_THREADS, (L.nlev + kc - 1) / kc);
+        mg::k_apply_gcr<J><<<grid, mg::RED_THREADS, 0, s>>>(L, z, w, h->W, h->glen, h->r, kc, h->partials,
+                                                            h->tickets + TK_SUMS, h->gs);
+        CK(cudaGetLastError());
+        return MG_OK;
+    }
+};
+
+template <int J>
+struct RunOrth {
+    static mg_status run(mg_handle* h, size_t n, cudaStream_t s) {
+        Prof pr(h, MG_K_GCR_ORTH, 0, 8.0 * n * (J > 0 ? J + 4 : 3), s);
+        mg::k_gcr_orth_update<J><<<h->red_grid, mg::RED_THREADS, 0, s>>>(n, h->W, h->glen, h->r, h->partials,
+                                                                         h->tickets + TK_ORTH, h->gs);
+        CK(cudaGetLastError());
+        return MG_OK;
+    }
+};
+
+template <int J>
+struct RunXupd {
+    static mg_status run(mg_handle* h, size_t n, double* x, cudaStream_t s) {
+        Prof pr(h, MG_K_GCR_UPDATE, 0, 8.0 * n * (J + 3), s);
+        mg::k_gcr_xupdate<J><<<h->red_grid, mg::RED_THREADS, 0, s>>>(n, x, h->Z, h->glen, h->gs);
+        CK(cudaGetLastError());
+        return MG_OK;
+    }
+};
 
 mg_status gcr_sums(mg_handle* h, size_t n, const double* w, int j, cudaStream_t s) {
-    if (j <= 4) return launch_gcr_sums<4>(h, n, w, j, s);
-    if (j <= 8) return launch_gcr_sums<8>(h, n, w, j, s);
-    return launch_gcr_sums<mg::MAXR>(h, n, w, j, s);
-}
-
-template <int JM>
-mg_status launch_apply_gcr(mg_handle* h, const double* z, double* w, int j, cudaStream_t s) {
-    const Lvl<double, double> L = View<double, double>::lvl(h, 0);
-    const double nc = (double)L.nlev * L.ncol;
-    Prof pr(h, MG_K_APPLY, 0, nc * 8.0 * (1 + 3 + 1 + 1 + j), s);   // z, 3 coefficients, w, r, w_i
-    const int kc = APPLY_KCHUNK;
-    dim3 grid((L.ncol + mg::RED_THREADS - 1) / mg::RED_THREADS, (L.nlev + kc - 1) / kc);
-    mg::k_apply_gcr<JM><<<grid, mg::RED_THREADS, 0, s>>>(L, z, w, h->W, h->glen, j, h->r, kc, h->partials,
-                                                         h->tickets + TK_SUMS, h->gs);
-    CK(cudaGetLastError());
-    return MG_OK;
+    return dispatch_j<RunSums>(j, h, n, w, s);
 }
 
 mg_status apply_gcr(mg_handle* h, const double* z, double* w, int j, cudaStream_t s) {
-    if (j <= 4) return launch_apply_gcr<4>(h, z, w, j, s);
-    if (j <= 8) return launch_apply_gcr<8>(h, z, w, j, s);
-    return launch_apply_gcr<mg::MAXR>(h, z, w, j, s);
+    return dispatch_j<RunApplyGcr>(j, h, z, w, s);
 }
 
 template <typename ApplyAS, typename ApplyP>
@@ -434,12 +477,7 @@ mg_status gcr(mg_handle* h, size_t n, const double* b, double* x, double tol, mg
             double* w = h->W + (size_t)j * h->glen;
             TRY(applyP(h->r, z));
             TRY(applyAS(z, w, j));
-            {
-                Prof pr(h, MG_K_GCR_ORTH, 0, 8.0 * n * (j > 0 ? j + 4 : 3), s);
-                mg::k_gcr_orth_update<<<G, mg::RED_THREADS, 0, s>>>(n, h->W, h->glen, j, h->r, h->partials,
-                                                                     h->tickets + TK_ORTH, h->gs);
-                CK(cudaGetLastError());
-            }
+            TRY(dispatch_j<RunOrth>(j, h, n, s));
             CK(cudaMemcpyAsync(h->host_sc, &h->gs->rr, sizeof(double), cudaMemcpyDeviceToHost, s));
             CK(cudaStreamSynchronize(s));
             ++it;
@@ -450,11 +488,7 @@ mg_status gcr(mg_handle* h, size_t n, const double* b, double* x, double tol, mg
             }
             rel = std::sqrt(rr / bb);
             const bool done = rel <= tol;
-            if (j == m - 1 || done || it == h->prm.max_iter) {
-                Prof pr(h, MG_K_GCR_UPDATE, 0, 8.0 * n * (j + 3), s);
-                mg::k_gcr_xupdate<<<G, mg::RED_THREADS, 0, s>>>(n, x, h->Z, h->glen, j, h->gs);
-                CK(cudaGetLastError());
-            }
+            if (j == m - 1 || done || it == h->prm.max_iter) TRY(dispatch_j<RunXupd>(j, h, n, x, s));
             if (done) {
                 st = MG_OK;
                 break;
@@ -664,7 +698,7 @@ mg_status setup_impl(mg_handle* h, const mg_mesh* mesh, const mg_params* prm, co
     TRY(dalloc(h, &h->gs, 1));
     {
         const size_t apply_blocks = (size_t)((ncol0 + mg::RED_THREADS - 1) / mg::RED_THREADS) *
-                                    ((nlev + APPLY_KCHUNK - 1) / APPLY_KCHUNK);
+                                    ((nlev + GCR_APPLY_KCHUNK - 1) / GCR_APPLY_KCHUNK);
         const size_t blocks = apply_blocks > (size_t)h->red_grid ? apply_blocks : (size_t)h->red_grid;
         h->npartials = blocks * (2 * mg::MAXR + 2);
         TRY(dalloc(h, &h->partials, h->npartials));
