@@ -10,6 +10,7 @@
 #pragma once
 
 #include <cuda_bf16.h>
+#include <cuda_pipeline.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -122,17 +123,16 @@ __global__ void __launch_bounds__(256) k_apply(Lvl<T, C> L, const X* __restrict_
 // thread per column this doubles the resident warps for the same stash and halves the
 // serial recurrence.
 //
-// Latency hiding: loads run ahead of use in register rings indexed statically (the step
-// loop is unrolled by the ring length): the streams first met in DRAM (the next iterate of
-// the own column, b, the E and N faces, the vertical face ahead) DEEP steps ahead; loads
-// that mostly hit in cache (W and S faces, neighbour iterates, prolongation) SHAL ahead.
-template <typename T>
-struct SweepDeep {
-    T xn, b, te, tn, tv;
-};
+// Latency hiding: the streams first met in DRAM (the next iterate of the own column, b,
+// the E and N faces and the vertical face ahead) are copied DEEP steps ahead into a
+// per-thread shared-memory ring with asynchronous copies (cp.async via the CUDA pipeline
+// primitives), so they occupy no registers while in flight; loads that mostly hit in cache
+// (W and S faces, neighbour iterates, prolongation terms) run SHAL steps ahead in a
+// register ring.  Both rings are indexed statically: the step loop is unrolled by DEEP.
 template <typename T>
 struct SweepShal {
-    T xh[4], tw, ts, cn, ch[4];
+    T xh[4], tw, ts, ch[4];
+    T te, tn, tv;   // coefficients narrower than 4 bytes (BF16) travel here instead
 };
 
 template <typename T, typename C, int MODE, typename X, typename B, typename O, bool BCOPY, int DEEP, int SHAL>
@@ -140,18 +140,29 @@ __global__ void k_sweep(Lvl<T, C> L, const X* __restrict__ x, const T* __restric
                         int ncol_c, const B* __restrict__ b, T* __restrict__ bcopy,
                         O* __restrict__ xo, T omega) {
     static_assert(DEEP % SHAL == 0, "ring lengths");
+    static_assert(sizeof(X) == sizeof(T), "iterate type");
+    // asynchronous copies move 4, 8 or 16 bytes: BF16 coefficients use the register ring
+    constexpr bool ASYNC_C = sizeof(C) >= 4;
     constexpr bool PRO = (MODE == XM_PROLONG || MODE == XM_PROLONG0);
     constexpr bool RAW = (MODE == XM_PLAIN || MODE == XM_PROLONG);   // reads the fine iterate
-    extern __shared__ unsigned char smem_raw[];
+    extern __shared__ __align__(16) unsigned char smem_raw[];
     const int nlev = L.nlev, hsteps = (nlev + 1) >> 1;
-    T* sc = reinterpret_cast<T*>(smem_raw);
-    T* se = sc + (size_t)hsteps * blockDim.x;
+    const int tid = threadIdx.x, bd = blockDim.x;
+    // shared memory: [ring of DEEP slots of b (B), xn (T), te, tn, tv (C, when staged)]
+    // [stash 2 x hsteps (T)]
+    B* rb = reinterpret_cast<B*>(smem_raw);
+    T* rx = reinterpret_cast<T*>(rb + (size_t)DEEP * bd);
+    C* rte = reinterpret_cast<C*>(rx + (size_t)DEEP * bd);
+    C* rtn = rte + (size_t)DEEP * bd;
+    C* rtv = rtn + (size_t)DEEP * bd;
+    T* sc = reinterpret_cast<T*>(ASYNC_C ? (unsigned char*)(rtv + (size_t)DEEP * bd)
+                                         : (unsigned char*)rte);
+    T* se = sc + (size_t)hsteps * bd;
     const int lane = threadIdx.x & 31;
     const bool upper = lane >= 16;
-    const int c_raw = blockIdx.x * (blockDim.x >> 1) + (threadIdx.x >> 5) * 16 + (lane & 15);
+    const int c_raw = blockIdx.x * (bd >> 1) + (threadIdx.x >> 5) * 16 + (lane & 15);
     const bool active = c_raw < L.ncol;
     const int c = active ? c_raw : L.ncol - 1;
-    const int tid = threadIdx.x, bd = blockDim.x;
     const int nsteps = upper ? nlev - hsteps : hsteps;
     const int dir = upper ? -1 : 1;
     const int kfirst = upper ? nlev - 1 : 0;
@@ -171,17 +182,24 @@ __global__ void k_sweep(Lvl<T, C> L, const X* __restrict__ x, const T* __restric
 
     // step i works on level kfirst + dir * i; the vertical face towards the next level in
     // the walk is Tv[k+1] going up and Tv[k] going down
-    auto load_deep = [&](int i, SweepDeep<T>& d) {
-        const int k = kfirst + dir * i;
-        const int kn = k + dir;
-        const size_t o = (size_t)k * ncol;
-        const C* th = L.Th + (size_t)k * nf;
-        if (RAW) d.xn = (kn >= 0 && kn < nlev) ? ldx<T>(x + (size_t)kn * ncol + c) : T(0);
-        if (PRO) d.xn += (kn >= 0 && kn < nlev) ? __ldg(xc + (size_t)kn * ncol_c + pc) : T(0);
-        d.b = (T)__ldg(b + o + c);
-        d.te = ldc<T>(th + fo[0]);
-        d.tn = ldc<T>(th + fo[2]);
-        d.tv = ldc<T>(L.Tv + (size_t)(upper ? k : k + 1) * ncol + c);
+    auto stage = [&](int i, int slot) {
+        if (i < nsteps) {
+            const int k = kfirst + dir * i;
+            const int kn = k + dir;
+            const size_t o = (size_t)k * ncol, so = (size_t)slot * bd + tid;
+            const C* th = L.Th + (size_t)k * nf;
+            __pipeline_memcpy_async(rb + so, b + o + c, sizeof(B));
+            if (RAW) {
+                const bool in = kn >= 0 && kn < nlev;
+                __pipeline_memcpy_async(rx + so, x + (size_t)(in ? kn : k) * ncol + c, sizeof(T), in ? 0 : sizeof(T));
+            }
+            if (ASYNC_C) {
+                __pipeline_memcpy_async(rte + so, th + fo[0], sizeof(C));
+                __pipeline_memcpy_async(rtn + so, th + fo[2], sizeof(C));
+                __pipeline_memcpy_async(rtv + so, L.Tv + (size_t)(upper ? k : k + 1) * ncol + c, sizeof(C));
+            }
+        }
+        __pipeline_commit();
     };
     auto load_shal = [&](int i, SweepShal<T>& d) {
         const int k = kfirst + dir * i;
@@ -197,13 +215,16 @@ __global__ void k_sweep(Lvl<T, C> L, const X* __restrict__ x, const T* __restric
         }
         d.tw = ldc<T>(th + fo[1]);
         d.ts = ldc<T>(th + fo[3]);
+        if (!ASYNC_C) {
+            d.te = ldc<T>(th + fo[0]);
+            d.tn = ldc<T>(th + fo[2]);
+            d.tv = ldc<T>(L.Tv + (size_t)(upper ? k : k + 1) * ncol + c);
+        }
     };
 
-    SweepDeep<T> dr[DEEP];
-    SweepShal<T> sr[SHAL];
 #pragma unroll
-    for (int j = 0; j < DEEP; ++j)
-        if (j < nsteps) load_deep(j, dr[j]);
+    for (int j = 0; j < DEEP; ++j) stage(j, j);
+    SweepShal<T> sr[SHAL];
 #pragma unroll
     for (int j = 0; j < SHAL; ++j)
         if (j < nsteps) load_shal(j, sr[j]);
@@ -215,12 +236,30 @@ __global__ void k_sweep(Lvl<T, C> L, const X* __restrict__ x, const T* __restric
 #pragma unroll
         for (int j = 0; j < DEEP; ++j) {
             const int i = i0 + j;
+            __pipeline_wait_prior(DEEP - 1);
+            const size_t so = (size_t)j * bd + tid;
+            const T bk = (T)rb[so];
+            T xn = RAW ? rx[so] : T(0);
+            T te = T(0), tn = T(0), tv = T(0);
+            if (ASYNC_C) {
+                te = (T)rte[so];
+                tn = (T)rtn[so];
+                tv = (T)rtv[so];
+            }
+            stage(i + DEEP, j);
             if (i < nsteps) {
-                const SweepDeep<T> d = dr[j];
                 const SweepShal<T> e = sr[j % SHAL];
-                if (i + DEEP < nsteps) load_deep(i + DEEP, dr[j]);
+                if (!ASYNC_C) {
+                    te = e.te;
+                    tn = e.tn;
+                    tv = e.tv;
+                }
                 if (i + SHAL < nsteps) load_shal(i + SHAL, sr[j % SHAL]);
                 const int k = kfirst + dir * i;
+                if (PRO) {
+                    const int kn = k + dir;
+                    if (kn >= 0 && kn < nlev) xn += __ldg(xc + (size_t)kn * ncol_c + pc);
+                }
                 T xh[4] = {T(0), T(0), T(0), T(0)};
                 if (RAW) {
 #pragma unroll
@@ -231,40 +270,40 @@ __global__ void k_sweep(Lvl<T, C> L, const X* __restrict__ x, const T* __restric
                     for (int s = 0; s < 4; ++s) xh[s] += e.ch[s];
                 }
                 const T rdz = __ldg(L.rdz + k);
-                if (BCOPY) bcopy[(size_t)k * ncol + c] = d.b;
-                T r = d.b;
+                if (BCOPY) bcopy[(size_t)k * ncol + c] = bk;
+                T r = bk;
                 if (MODE != XM_ZERO) {
-                    T hx = d.te * (x0 - xh[0]);
+                    T hx = te * (x0 - xh[0]);
                     hx += e.tw * (x0 - xh[1]);
-                    hx += d.tn * (x0 - xh[2]);
+                    hx += tn * (x0 - xh[2]);
                     hx += e.ts * (x0 - xh[3]);
-                    r -= x0 + (rA * hx + rdz * (d.tv * (x0 - d.xn) + tprev * (x0 - xprev)));
+                    r -= x0 + (rA * hx + rdz * (tv * (x0 - xn) + tprev * (x0 - xprev)));
                 }
-                anext = rdz * d.tv;
+                anext = rdz * tv;
                 const T m = (rdz * tprev) * ip;
-                q = (T(1) + rA * ((d.te + e.tw) + (d.tn + e.ts))) + m * q;
+                q = (T(1) + rA * ((te + e.tw) + (tn + e.ts))) + m * q;
                 const T p = q + anext;
                 y = r + m * y;
                 ip = T(1) / p;
                 sc[(size_t)i * bd + tid] = y * ip;
                 se[(size_t)i * bd + tid] = anext * ip;
                 xprev = x0;
-                x0 = d.xn;
-                tprev = d.tv;
+                x0 = xn;
+                tprev = tv;
             }
         }
     }
+    __pipeline_wait_prior(0);
     // interface rows h-1 (lower half) and h (upper half)
     const T qo = __shfl_xor_sync(0xffffffffu, q, 16);
     const T yo = __shfl_xor_sync(0xffffffffu, y, 16);
     const T ao = __shfl_xor_sync(0xffffffffu, anext, 16);
     T dlt;
     if (nlev - hsteps == 0) {
-        dlt = y * ip;   // single level: nothing above, anext = 0
+        dlt = y * ip;   // a single level: nothing above, anext = 0
     } else {
-        const T po = qo + ao, pm = q + anext;
+        const T po = qo + ao;
         dlt = (y * po + anext * yo) / (q * po + anext * qo);
-        (void)pm;
     }
     if (!active || nsteps == 0) return;
     {

@@ -238,14 +238,18 @@ mg_status launch_sweep(mg_handle* h, int lev, const Lvl<T, C>& L, const X* x, co
     if (MODE == mg::XM_PROLONG || MODE == mg::XM_PROLONG0) per += 0.25 * sizeof(T);
     if (BCOPY) per += sizeof(T);
     Prof pr(h, MG_K_SWEEP, lev, nc * per, s);
-    // two threads per column; the stash (2 values per step of half a column per thread)
-    // must fit the shared-memory budget
+    // two threads per column; per thread the shared memory holds the asynchronous-copy
+    // ring (DEEP slots of b, the next iterate and, unless BF16, three coefficients) and the
+    // stash (2 values per step of half a column); it must fit the budget
+    constexpr int DEEP = SweepPF<T>::deep;
     const int hsteps = (L.nlev + 1) / 2;
+    const size_t per_thread = DEEP * (sizeof(B) + sizeof(T) + (sizeof(C) >= 4 ? 3 * sizeof(C) : 0)) +
+                              2 * (size_t)hsteps * sizeof(T);
     int bd = sweep_block(2 * L.ncol);
-    const int cap = (int)(SWEEP_SMEM_MAX / (2 * (size_t)hsteps * sizeof(T))) / 32 * 32;
+    const int cap = (int)(SWEEP_SMEM_MAX / per_thread) / 32 * 32;
     if (cap < 32) return MG_ERR_UNSUPPORTED;
     if (bd > cap) bd = cap;
-    const size_t smem = 2 * (size_t)hsteps * bd * sizeof(T);
+    const size_t smem = per_thread * bd;
     if (smem > 48 * 1024)
         CK(cudaFuncSetAttribute(mg::k_sweep<T, C, MODE, X, B, O, BCOPY, SweepPF<T>::deep, SweepPF<T>::shal>,
                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
@@ -264,7 +268,9 @@ mg_status launch_restrict(mg_handle* h, int lev, const Lvl<T, C>& L, const X* x,
     Prof pr(h, MG_K_RESTRICT, lev, nc * (sizeof(B) + 3 * sizeof(C) + (XZERO ? 0 : sizeof(X)) + 0.25 * sizeof(O) +
                                           sizeof(T) / (double)L.nlev), s);
     const int bd = ncol_c >= 128 * 300 ? 128 : (ncol_c >= 64 * 300 ? 64 : 32);
-    const int kc = APPLY_KCHUNK;
+    // chunk of levels per thread: enough threads to fill the GPU, few re-loads of the
+    // 32 connectivity entries of the 4 children
+    const int kc = ncol_c >= 128 * 300 ? 3 * APPLY_KCHUNK : APPLY_KCHUNK;
     const dim3 grid((ncol_c + bd - 1) / bd, (L.nlev + kc - 1) / kc);
     mg::k_resid_restrict<T, C, XZERO, X, B, O><<<grid, bd, 0, s>>>(L, x, b, w, bc, ncol_c, kc);
     CK(cudaGetLastError());
