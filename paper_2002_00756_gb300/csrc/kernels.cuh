@@ -116,22 +116,26 @@ __global__ void __launch_bounds__(256) k_apply(Lvl<T, C> L, const X* __restrict_
 //     m = a_prev / p_prev,  q = s + m q_prev,  p = q + a_next,  y = r + m y_prev
 // (s = 1 + horizontal coefficients: pivots are sums of positive terms).  The two halves
 // meet at rows h-1 and h; their 2x2 system
-//     [p_A  -a_A] [x_A]   [y_A]
-//     [-a_B  p_B] [x_B] = [y_B],   det = q_A p_B + a_A q_B  (no cancellation)
+//     [p_A  -a_A] [d_A]   [y_A]
+//     [-a_B  p_B] [d_B] = [y_B],   det = q_A p_B + a_A q_B  (no cancellation)
 // is solved by both lanes after a shuffle, then each half back-substitutes towards its
-// end.  Per step the thread stashes y/p and a_next/p in shared memory.  Compared with one
-// thread per column this doubles the resident warps for the same stash and halves the
-// serial recurrence.
+// end: d_i = y_i/p_i + e_i d_{i+1}, e_i = a_next/p_i, out_i = x_i + omega d_i.  The back
+// substitution runs directly on the output,
+//     out_i = w_i + e_i out_{i+1},   w_i = x_i + omega y_i/p_i - e_i x_{i+1},
+// so the forward pass stashes (w_i, e_i) in shared memory and the iterate is never read
+// again.  Compared with one thread per column this doubles the resident warps for the
+// same stash and halves the serial recurrence.
 //
 // Latency hiding: the streams first met in DRAM (the next iterate of the own column, b,
 // the E and N faces and the vertical face ahead) are copied DEEP steps ahead into a
 // per-thread shared-memory ring with asynchronous copies (cp.async via the CUDA pipeline
 // primitives), so they occupy no registers while in flight; loads that mostly hit in cache
 // (W and S faces, neighbour iterates, prolongation terms) run SHAL steps ahead in a
-// register ring.  Both rings are indexed statically: the step loop is unrolled by DEEP.
+// register ring, with 1/dz of the level.  Both rings are indexed statically: the step loop
+// is unrolled by DEEP.
 template <typename T>
 struct SweepShal {
-    T xh[4], tw, ts, ch[4];
+    T xh[4], tw, ts, ch[4], cn, rdz;
     T te, tn, tv;   // coefficients narrower than 4 bytes (BF16) travel here instead
 };
 
@@ -212,9 +216,12 @@ __global__ void k_sweep(Lvl<T, C> L, const X* __restrict__ x, const T* __restric
         if (PRO) {
 #pragma unroll
             for (int s = 0; s < 4; ++s) d.ch[s] = __ldg(xc + oc + pn[s]);
+            const int kn = k + dir;
+            d.cn = (kn >= 0 && kn < nlev) ? __ldg(xc + (size_t)kn * ncol_c + pc) : T(0);
         }
         d.tw = ldc<T>(th + fo[1]);
         d.ts = ldc<T>(th + fo[3]);
+        d.rdz = __ldg(L.rdz + k);
         if (!ASYNC_C) {
             d.te = ldc<T>(th + fo[0]);
             d.tn = ldc<T>(th + fo[2]);
@@ -256,10 +263,7 @@ __global__ void k_sweep(Lvl<T, C> L, const X* __restrict__ x, const T* __restric
                 }
                 if (i + SHAL < nsteps) load_shal(i + SHAL, sr[j % SHAL]);
                 const int k = kfirst + dir * i;
-                if (PRO) {
-                    const int kn = k + dir;
-                    if (kn >= 0 && kn < nlev) xn += __ldg(xc + (size_t)kn * ncol_c + pc);
-                }
+                if (PRO) xn += e.cn;
                 T xh[4] = {T(0), T(0), T(0), T(0)};
                 if (RAW) {
 #pragma unroll
@@ -269,7 +273,7 @@ __global__ void k_sweep(Lvl<T, C> L, const X* __restrict__ x, const T* __restric
 #pragma unroll
                     for (int s = 0; s < 4; ++s) xh[s] += e.ch[s];
                 }
-                const T rdz = __ldg(L.rdz + k);
+                const T rdz = e.rdz;
                 if (BCOPY) bcopy[(size_t)k * ncol + c] = bk;
                 T r = bk;
                 if (MODE != XM_ZERO) {
@@ -285,8 +289,9 @@ __global__ void k_sweep(Lvl<T, C> L, const X* __restrict__ x, const T* __restric
                 const T p = q + anext;
                 y = r + m * y;
                 ip = T(1) / p;
-                sc[(size_t)i * bd + tid] = y * ip;
-                se[(size_t)i * bd + tid] = anext * ip;
+                const T ei = anext * ip;
+                sc[(size_t)i * bd + tid] = x0 + omega * (y * ip) - ei * xn;
+                se[(size_t)i * bd + tid] = ei;
                 xprev = x0;
                 x0 = xn;
                 tprev = tv;
@@ -306,17 +311,13 @@ __global__ void k_sweep(Lvl<T, C> L, const X* __restrict__ x, const T* __restric
         dlt = (y * po + anext * yo) / (q * po + anext * qo);
     }
     if (!active || nsteps == 0) return;
-    {
-        const int k = kfirst + dir * (nsteps - 1);
-        const size_t o = (size_t)k * ncol, oc = (size_t)k * ncol_c;
-        xo[o + c] = (O)(xval<MODE, T>(x, xc, o, oc, c, pc) + omega * dlt);
-    }
+    // xprev holds the iterate at the last level of this half: out = x + omega d there
+    T out = xprev + omega * dlt;
+    xo[(size_t)(kfirst + dir * (nsteps - 1)) * ncol + c] = (O)out;
 #pragma unroll 4
     for (int i = nsteps - 2; i >= 0; --i) {
-        dlt = sc[(size_t)i * bd + tid] + se[(size_t)i * bd + tid] * dlt;
-        const int k = kfirst + dir * i;
-        const size_t o = (size_t)k * ncol, oc = (size_t)k * ncol_c;
-        xo[o + c] = (O)(xval<MODE, T>(x, xc, o, oc, c, pc) + omega * dlt);
+        out = sc[(size_t)i * bd + tid] + se[(size_t)i * bd + tid] * out;
+        xo[(size_t)(kfirst + dir * i) * ncol + c] = (O)out;
     }
 }
 
@@ -373,6 +374,89 @@ __global__ void __launch_bounds__(128) k_resid_restrict(Lvl<T, C> L, const X* __
             acc += wq[q] * r;
         }
         bc[(size_t)k * ncol_c + Cc] = (O)acc;
+    }
+}
+
+// Residual and restriction, one thread per fine column (for n divisible by 16): a warp
+// covers fine columns i0..i0+15 of rows 2J (lanes 0-15) and 2J+1 (lanes 16-31) of one
+// panel, i.e. 8 coarse columns; the 2x2 sums of w_child r_child are two shuffles.  Each
+// thread walks kchunk levels with loads issued SHAL levels ahead in a register ring.
+template <typename T, typename C, bool XZERO, typename X, typename B, typename O, int SHAL>
+__global__ void __launch_bounds__(128) k_resid_restrict16(Lvl<T, C> L, const X* __restrict__ x,
+                                                           const B* __restrict__ b,
+                                                           const T* __restrict__ w,
+                                                           O* __restrict__ bc, int ncol_c, int kchunk) {
+    const int n = L.n, nc = n >> 1, tiles = n >> 4;
+    const int warp = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int nwarps = 6 * nc * tiles;   // (panel, coarse row, tile)
+    const int lane = threadIdx.x & 31;
+    const bool valid = warp < nwarps;
+    const int wq = valid ? warp : 0;
+    const int p = wq / (nc * tiles), rem = wq - p * nc * tiles, J = rem / tiles, t = rem - J * tiles;
+    const int rowf = 2 * J + (lane >> 4), i = t * 16 + (lane & 15);
+    const int c = p * n * n + rowf * n + i;
+    const int Cc = p * nc * nc + J * nc + (i >> 1);
+    const int q = ((lane >> 4) << 1) | (i & 1);   // child index 2b + a
+    const size_t ncol = L.ncol, nf = 2 * ncol;
+    const int k0 = blockIdx.y * kchunk;
+    const int k1 = min(L.nlev, k0 + kchunk);
+    int nb[4], fo[4];
+#pragma unroll
+    for (int s = 0; s < 4; ++s) {
+        nb[s] = __ldg(L.nbr + s * ncol + c);
+        fo[s] = __ldg(L.fof + s * ncol + c);
+    }
+    const T rA = __ldg(L.rA + c);
+    const T wc = __ldg(w + (size_t)q * ncol_c + Cc);
+    struct Lv {
+        T xp, xn[4], b, th[4], tup, rdz;
+    };
+    auto load = [&](int k, Lv& d) {
+        const size_t o = (size_t)k * ncol;
+        if (!XZERO) {
+            d.xp = (k + 1 < L.nlev) ? ldx<T>(x + o + ncol + c) : T(0);
+#pragma unroll
+            for (int s = 0; s < 4; ++s) d.xn[s] = ldx<T>(x + o + nb[s]);
+        }
+        const C* th = L.Th + (size_t)k * nf;
+#pragma unroll
+        for (int s = 0; s < 4; ++s) d.th[s] = ldc<T>(th + fo[s]);
+        d.tup = ldc<T>(L.Tv + o + ncol + c);
+        d.b = (T)__ldg(b + o + c);
+        d.rdz = __ldg(L.rdz + k);
+    };
+    Lv ring[SHAL];
+#pragma unroll
+    for (int j = 0; j < SHAL; ++j)
+        if (k0 + j < k1) load(k0 + j, ring[j]);
+    T xm = (XZERO || k0 == 0) ? T(0) : ldx<T>(x + (size_t)(k0 - 1) * ncol + c);
+    T x0 = XZERO ? T(0) : ldx<T>(x + (size_t)k0 * ncol + c);
+    T tdn = ldc<T>(L.Tv + (size_t)k0 * ncol + c);
+    for (int kb = k0; kb < k1; kb += SHAL) {
+#pragma unroll
+        for (int j = 0; j < SHAL; ++j) {
+            const int k = kb + j;
+            if (k < k1) {
+                const Lv d = ring[j];
+                if (k + SHAL < k1) load(k + SHAL, ring[j]);
+                T r = d.b;
+                if (!XZERO) {
+                    T h = d.th[0] * (x0 - d.xn[0]);
+                    h += d.th[1] * (x0 - d.xn[1]);
+                    h += d.th[2] * (x0 - d.xn[2]);
+                    h += d.th[3] * (x0 - d.xn[3]);
+                    r -= x0 + (rA * h + d.rdz * (d.tup * (x0 - d.xp) + tdn * (x0 - xm)));
+                    xm = x0;
+                    x0 = d.xp;
+                }
+                tdn = d.tup;
+                // sum the 4 children in the order (a=0,b=0)+(a=1,b=0) + (a=0,b=1)+(a=1,b=1)
+                T v = wc * r;
+                v += __shfl_xor_sync(0xffffffffu, v, 1);
+                v += __shfl_xor_sync(0xffffffffu, v, 16);
+                if (valid && (lane & 17) == 0) bc[(size_t)k * ncol_c + Cc] = (O)v;
+            }
+        }
     }
 }
 

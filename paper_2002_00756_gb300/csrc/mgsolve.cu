@@ -17,6 +17,17 @@
 #include "krylov.cuh"
 #include "mesh.h"
 
+// tuning knobs of the sweep kernel (FP32 prefetch depths, threads per block)
+#ifndef MG_SWEEP_DEEP32
+#define MG_SWEEP_DEEP32 4
+#endif
+#ifndef MG_SWEEP_SHAL32
+#define MG_SWEEP_SHAL32 4
+#endif
+#ifndef MG_SWEEP_BLOCK
+#define MG_SWEEP_BLOCK 128
+#endif
+
 using mg::Lvl;
 typedef __nv_bfloat16 bf16;
 
@@ -204,7 +215,7 @@ struct View<float, bf16> {
 constexpr size_t SWEEP_SMEM_MAX = 200 * 1024;
 
 inline int sweep_block(int ncol) {
-    if (ncol >= 128 * 300) return 128;
+    if (ncol >= 128 * 300) return MG_SWEEP_BLOCK;
     if (ncol >= 64 * 300) return 64;
     return 32;
 }
@@ -225,8 +236,8 @@ mg_status launch_apply(mg_handle* h, int lev, const Lvl<T, C>& L, const X* x, Y*
 // prefetch depths of the sweep's register rings (levels in flight per thread)
 template <typename T>
 struct SweepPF {
-    static constexpr int deep = sizeof(T) == 8 ? 4 : 8;
-    static constexpr int shal = sizeof(T) == 8 ? 2 : 4;
+    static constexpr int deep = sizeof(T) == 8 ? 4 : MG_SWEEP_DEEP32;
+    static constexpr int shal = sizeof(T) == 8 ? 2 : MG_SWEEP_SHAL32;
 };
 
 template <typename T, typename C, int MODE, typename X, typename B, typename O, bool BCOPY>
@@ -267,6 +278,15 @@ mg_status launch_restrict(mg_handle* h, int lev, const Lvl<T, C>& L, const X* x,
     const double nc = (double)L.nlev * L.ncol;
     Prof pr(h, MG_K_RESTRICT, lev, nc * (sizeof(B) + 3 * sizeof(C) + (XZERO ? 0 : sizeof(X)) + 0.25 * sizeof(O) +
                                           sizeof(T) / (double)L.nlev), s);
+    if (L.n % 16 == 0) {
+        // one thread per fine column, 4 warps per block
+        const int warps = 6 * (L.n / 2) * (L.n / 16);
+        const int kc = APPLY_KCHUNK;
+        const dim3 grid((warps + 3) / 4, (L.nlev + kc - 1) / kc);
+        mg::k_resid_restrict16<T, C, XZERO, X, B, O, 2><<<grid, 128, 0, s>>>(L, x, b, w, bc, ncol_c, kc);
+        CK(cudaGetLastError());
+        return MG_OK;
+    }
     const int bd = ncol_c >= 128 * 300 ? 128 : (ncol_c >= 64 * 300 ? 64 : 32);
     // chunk of levels per thread: enough threads to fill the GPU, few re-loads of the
     // 32 connectivity entries of the 4 children
