@@ -183,6 +183,30 @@ mg_status mixed_apply(mg_handle* h, const double* u, const double* p, double* yu
 mg_status schur_precond(mg_handle* h, const double* ru, const double* rp, double* u, double* p,
                         void* stream);
 
+/* ---- block-Jacobi smoothing that allocates nothing ----
+ * The paper has no counterpart to this call: it is a service for callers that cannot
+ * allocate device memory at the point where they smooth, for instance code being
+ * recorded into a CUDA graph (an allocation there would end the capture), a real-time
+ * loop that must not enter the allocator, or a host framework whose memory pool owns
+ * all device memory after start-up.
+ *
+ * It computes exactly what mg_smooth computes (same kernels, same order), but it neither
+ * allocates nor touches the handle's workspace: intermediate iterates are kept in one
+ * fixed device array inside the library of MG_NOALLOC_MAX_CELLS doubles (16 MiB), which
+ * every GPU that loads the library holds until the process exits.  Levels with more than
+ * MG_NOALLOC_MAX_CELLS cells (nlev * 6 (n / 2^level)^2) are rejected with MG_ERR_ARG.
+ * The handle itself still comes from mg_setup.
+ *   - The first call on a device looks up the array's device address (with that device
+ *     current), so make that first call before any stream capture begins.
+ *   - All calls share the one array: calls that overlap on the GPU (on different streams,
+ *     or from different threads without ordering) race with each other and must be
+ *     serialised by the caller.  The array keeps the last call's contents; nothing in it
+ *     needs to start at zero, because every sweep writes all its cells before any is read.
+ * Arguments as for mg_smooth (x_in == NULL: zero initial guess; x_in may equal x_out). */
+#define MG_NOALLOC_MAX_CELLS (1 << 21)
+mg_status mg_smooth_noalloc(mg_handle* h, int32_t level, const double* b, const double* x_in,
+                            double* x_out, int32_t sweeps, void* stream);
+
 /* ---- per-launch profiling ----
  * While profiling is on, every kernel launch made by the calls above is bracketed by two
  * CUDA events on its stream, and its kind, multigrid level and algorithmic traffic (every

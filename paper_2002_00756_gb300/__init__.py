@@ -74,6 +74,7 @@ _SIGS = {
     "mixed_solve": [_VP, _DP, _DP, _DP, _DP, _D, ctypes.POINTER(_Info), _VP],
     "mg_level_apply": [_VP, _I32, _DP, _DP, _VP],
     "mg_smooth": [_VP, _I32, _DP, _DP, _DP, _I32, _VP],
+    "mg_smooth_noalloc": [_VP, _I32, _DP, _DP, _DP, _I32, _VP],
     "mg_residual_restrict": [_VP, _I32, _DP, _DP, _DP, _VP],
     "mg_prolong_add": [_VP, _I32, _DP, _DP, _VP],
     "mixed_apply": [_VP, _DP, _DP, _DP, _DP, _VP],
@@ -266,6 +267,21 @@ def mg_smooth(h: Handle, level: int, b, x_in, x_out, sweeps: int, stream=None):
     xin = None if x_in is None else _ptr(x_in, n, "x_in")
     _check(load().mg_smooth(h.ptr, level, _ptr(b, n, "b"), xin, _ptr(x_out, n, "x_out"), sweeps, _stream(stream)),
            "mg_smooth")
+
+
+MG_NOALLOC_MAX_CELLS = 1 << 21
+
+
+def mg_smooth_noalloc(h: Handle, level: int, b, x_in, x_out, sweeps: int, stream=None):
+    """mg_smooth for callers that cannot allocate device memory at this point (code being
+    captured into a CUDA graph, real-time loops, frameworks owning all device memory): the
+    library keeps the intermediate iterate in a fixed 16 MiB device array, so this call
+    allocates nothing.  Levels above MG_NOALLOC_MAX_CELLS cells are rejected; overlapping
+    calls race on the shared array.  The first call on a device must precede any capture."""
+    n = h.level_cells(level)
+    xin = None if x_in is None else _ptr(x_in, n, "x_in")
+    _check(load().mg_smooth_noalloc(h.ptr, level, _ptr(b, n, "b"), xin, _ptr(x_out, n, "x_out"), sweeps,
+                                    _stream(stream)), "mg_smooth_noalloc")
 
 
 def mg_residual_restrict(h: Handle, level: int, b, x, bc, stream=None):

@@ -7,6 +7,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <string>
 #include <utility>
@@ -947,3 +948,71 @@ mg_status mg_profile_stop(mg_handle* h, mg_kernel_record* out, int32_t cap, int3
 }
 
 }  // extern "C"
+
+// =====================================================================================
+// Block-Jacobi smoothing without allocation (see mg_smooth_noalloc in mgsolve.h).
+//
+// The intermediate iterates that mg_smooth keeps in the handle's workspace live here in
+// one fixed device array instead.  Every GPU that loads this library holds the array until
+// the process exits, and every call shares it.
+static __device__ __align__(256) double g_smooth_scratch[MG_NOALLOC_MAX_CELLS];
+
+namespace {
+// Host code cannot use g_smooth_scratch as a device address: on the host it names a
+// stand-in object.  Its device address is looked up once per device (with that device
+// current) and kept here.
+constexpr int kMaxDevices = 64;
+std::mutex g_scratch_mutex;
+double* g_scratch_addr[kMaxDevices] = {};
+
+mg_status scratch_address(int device, double** out) {
+    if (device < 0 || device >= kMaxDevices) return MG_ERR_UNSUPPORTED;
+    std::lock_guard<std::mutex> lock(g_scratch_mutex);
+    if (!g_scratch_addr[device]) {
+        void* p = nullptr;
+        const cudaError_t e = cudaGetSymbolAddress(&p, g_smooth_scratch);
+        if (e != cudaSuccess || !p) {
+            cudaGetLastError();
+            return MG_ERR_CUDA;
+        }
+        g_scratch_addr[device] = static_cast<double*>(p);
+    }
+    *out = g_scratch_addr[device];
+    return MG_OK;
+}
+}  // namespace
+
+extern "C" mg_status mg_smooth_noalloc(mg_handle* h, int32_t level, const double* b, const double* x_in,
+                                       double* x_out, int32_t sweeps, void* stream) {
+    TRY(check_level(h, level));
+    if (!b || !x_out || sweeps < 0 || b == x_out) return MG_ERR_ARG;
+    const size_t n = cells(h, level);
+    if (n > (size_t)MG_NOALLOC_MAX_CELLS) return MG_ERR_ARG;
+    DeviceGuard dg(h->device);
+    double* scratch = nullptr;
+    TRY(scratch_address(h->device, &scratch));
+    cudaStream_t s = S(stream);
+    const Lvl<double, double> L = View<double, double>::lvl(h, level);
+    if (sweeps == 0) {
+        if (!x_in) CK(cudaMemsetAsync(x_out, 0, n * sizeof(double), s));
+        else if (x_in != x_out) CK(cudaMemcpyAsync(x_out, x_in, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+        return MG_OK;
+    }
+    // Sweeps alternate between the scratch array and x_out, ordered so that the last one
+    // writes x_out.  A sweep never writes the array it reads, so when x_in aliases x_out
+    // and x_out would be the first target, the first sweep goes to the scratch array and
+    // the result is copied to x_out at the end.
+    bool to_out = ((sweeps - 1) % 2) == 0;
+    const bool copy_back = to_out && x_in == x_out;
+    if (copy_back) to_out = false;
+    const double* cur = x_in;
+    for (int i = 0; i < sweeps; ++i) {
+        double* dst = to_out ? x_out : scratch;
+        TRY((sweep_any<double, double, double, double>(nullptr, level, L, cur, (const double*)nullptr, 0, b,
+                                                       nullptr, dst, h->prm.omega, s)));
+        cur = dst;
+        to_out = !to_out;
+    }
+    if (cur != x_out) CK(cudaMemcpyAsync(x_out, cur, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    return MG_OK;
+}
