@@ -39,6 +39,33 @@ UNIT = "ms"
 WORKLOAD = "C192L70 pressure solve: GCR(5) FP64 outer + 4-level FP32 V-cycle, tol 1e-8"
 
 
+SWEEP_VARIANTS = ("plain", "zero", "prolong", "prolong0")
+
+
+def _source_digest() -> str:
+    """sha256 of the kernel sources: a committed ncu record is used only while it matches."""
+    import hashlib
+    hsh = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2002_00756_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        if f.endswith((".cu", ".cuh", ".h", ".cpp")):
+            hsh.update(open(os.path.join(csrc, f), "rb").read())
+    return hsh.hexdigest()
+
+
+def profiled_traffic(kernel: str, workload: str, precision: str):
+    """DRAM bytes (read + write) per launch from profiles/dram_traffic.json, if that record
+    was taken on the current kernel sources, else None."""
+    p = os.path.join(ROOT, "profiles", "dram_traffic.json")
+    if not os.path.exists(p):
+        return None
+    d = json.load(open(p))
+    if d.get("source_sha256") != _source_digest():
+        return None
+    rec = d.get("kernels", {}).get(f"{workload}/{precision}/{kernel}")
+    return None if rec is None else float(rec["dram_bytes_per_launch"])
+
+
 def _peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -121,39 +148,19 @@ def run_reference(args, cfg, inp, world, rank):
     hier = pressure_hierarchy(cfg, inp)
     H = hier.levels[0]
     P = hier.as_preconditioner(cfg.omega, cfg.n_pre, cfg.n_post, cfg.n_coarse)
+    from oracle.krylov import GCR
     b = inp["rhs"]
-    nb = np.linalg.norm(b)
     for _ in range(args.warmup):          # warm-up: one operator application each
         H.apply(b)
-
-    class Solve:
-        def __init__(self):
-            self.x = np.zeros_like(b)
-            self.r = b.copy()
-            self.Z, self.W, self.WW = [], [], []
-
-        def step(self):
-            z = np.asarray(P(self.r)).ravel().copy()
-            w = H.apply(z).ravel()
-            for zj, wj, wwj in zip(self.Z, self.W, self.WW):
-                beta = np.dot(w, wj) / wwj
-                w -= beta * wj
-                z -= beta * zj
-            ww = np.dot(w, w)
-            a = np.dot(self.r, w) / ww
-            self.x += a * z
-            self.r -= a * w
-            if len(self.Z) + 1 >= cfg.gcr_restart:
-                self.Z, self.W, self.WW = [], [], []
-            else:
-                self.Z.append(z)
-                self.W.append(w)
-                self.WW.append(ww)
-            return np.linalg.norm(self.r) / nb
+    Solve = lambda: GCR(H.apply, b, P, cfg.gcr_restart)
 
     s = Solve()
     its, times, per_solve_iters = 0, [], []
+    budget_s = 150.0       # the timed steps stop once this much CPU time is spent
+    t_start = time.perf_counter()
     for _ in range(args.steps):
+        if times and time.perf_counter() - t_start > budget_s:
+            break
         t0 = time.perf_counter()
         rel = s.step()
         times.append(time.perf_counter() - t0)
@@ -173,13 +180,15 @@ def run_reference(args, cfg, inp, world, rank):
     value = sec_it * n_it * 1e3
     line = {
         "impl": "reference", "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(sec_it * 1e3, 3),
+        "steps": len(times), "steps_requested": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(sec_it * 1e3, 3),
         "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic", "config": {"workload": WORKLOAD.replace("FP32 V-cycle", "FP64 V-cycle (CPU oracle)"),
                                         "n": cfg.n, "nlev": cfg.nlev, "levels": cfg.levels},
         "cpu_baseline": {"value": round(value, 3), "unit": UNIT, "cores": 1, "kind": "oracle",
-                         "sample": f"one numpy FP64 GCR iteration of the C192L70 solve per step; "
-                                   f"ms/solve = mean iteration time x {n_it:.1f} iterations ({how})"},
+                         "sample": f"one numpy FP64 GCR iteration of the C192L70 solve per step, "
+                                   f"{len(times)} steps timed (150 s budget); ms/solve = mean iteration "
+                                   f"time x {n_it:.1f} iterations ({how})"},
         "e2e": {"value": round(value, 3), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -275,16 +284,18 @@ def main():
 
     # ---- roofline of the dominant kernel (finest-level sweep) ----
     peak, peak_src = _peaks()
-    by = {}
+    by, byv = {}, {}
     for r in recs:
-        k = (r["kind"], r["level"])
-        a = by.setdefault(k, [0, 0.0, 0.0])
-        a[0] += 1
-        a[1] += r["ms"]
-        a[2] += r["bytes"]
-    top = max(by.items(), key=lambda kv: kv[1][1])
-    (kind, lev), (cnt, ms, byt) = top
+        for key, dct in (((r["kind"], r["level"]), by), ((r["kind"], r["level"], r["variant"]), byv)):
+            a = dct.setdefault(key, [0, 0.0, 0.0])
+            a[0] += 1
+            a[1] += r["ms"]
+            a[2] += r["bytes"]
+    # the dominant kernel: the single kernel (kind, level, variant) with the most time
+    (kind, lev, var), (cnt, ms, byt) = max(byv.items(), key=lambda kv: kv[1][1])
+    kname = f"{kind}@L{lev}" + (f"/{SWEEP_VARIANTS[var]}" if kind == "sweep" else "")
     achieved = byt / (ms * 1e-3) / 1e9
+    traffic = profiled_traffic(kname, cfg.name, args.precision)
     vc_kinds = ("sweep", "restrict", "prolong", "convert")
     vc_ms = sum(v[1] for k, v in by.items() if k[0] in vc_kinds)
     vc_bytes = sum(v[2] for k, v in by.items() if k[0] in vc_kinds)
@@ -307,9 +318,11 @@ def main():
                    "l2": "working set (~3 GB) larger than L2; no flush"},
         "e2e": {"value": round(e2e_ms, 4), "unit": UNIT, "h2d_bytes_per_step": int(b.numel() * 8),
                 "d2h_bytes_per_step": int(b.numel() * 8)},
-        "roofline": {"bound": "hbm", "kernel": f"{kind}@L{lev}", "achieved": round(achieved, 1), "peak": peak,
-                     "unit": "GB/s", "frac": round(achieved / peak, 4), "traffic": None,
-                     "peak_source": peak_src,
+        "roofline": {"bound": "hbm", "kernel": kname, "achieved": round(achieved, 1), "peak": peak,
+                     "unit": "GB/s", "frac": round(achieved / peak, 4),
+                     "traffic": None if traffic is None else round(traffic / 1e9 / (ms / cnt * 1e-3), 1),
+                     "traffic_bytes_per_launch": traffic, "algorithmic_bytes_per_launch": round(byt / cnt),
+                     "launch_us": round(ms / cnt * 1e3, 2), "peak_source": peak_src + " (MEASURED_PEAKS.json hbm_gbs)",
                      "vcycle_GBps": round(vc_bytes / (vc_ms * 1e-3) / 1e9, 1),
                      "vcycle_frac": round(vc_bytes / (vc_ms * 1e-3) / 1e9 / peak, 4)},
         "gpu_launches": len(recs),

@@ -227,6 +227,7 @@ enum {
 typedef struct {
     int32_t kind;      /* MG_K_* */
     int32_t level;     /* multigrid level (0 = finest) */
+    int32_t variant;   /* sweeps: iterate source, 0 plain, 1 zero, 2 prolongated, 3 prolongation only */
     double bytes;      /* algorithmic bytes of the launch */
     double ms;         /* event-timed duration */
 } mg_kernel_record;

@@ -25,40 +25,53 @@ from typing import Callable
 import numpy as np
 
 
-def gcr(A: Callable, b: np.ndarray, P: Callable | None = None, tol: float = 1e-8,
-        restart: int = 5, maxiter: int = 500):
-    """Solve A x = b; returns (x, iterations, relative residual history)."""
-    b = np.asarray(b, dtype=np.float64).ravel()
-    P = (lambda v: v) if P is None else P
-    x = np.zeros_like(b)
-    r = b.copy()
-    nb = np.linalg.norm(b)
-    hist = [1.0]
-    if nb == 0.0:
-        return x, 0, hist
-    Z, W, WW = [], [], []
-    it = 0
-    while it < maxiter:
-        z = np.asarray(P(r), dtype=np.float64).ravel().copy()
-        w = np.asarray(A(z), dtype=np.float64).ravel().copy()
-        for zj, wj, wwj in zip(Z, W, WW):
+class GCR:
+    """The iteration above, one step at a time: ``step()`` does one GCR iteration and
+    returns the new ||r|| / ||b||."""
+
+    def __init__(self, A: Callable, b: np.ndarray, P: Callable | None = None, restart: int = 5):
+        self.A = A
+        self.P = (lambda v: v) if P is None else P
+        self.b = np.asarray(b, dtype=np.float64).ravel()
+        self.restart = restart
+        self.x = np.zeros_like(self.b)
+        self.r = self.b.copy()
+        self.nb = np.linalg.norm(self.b)
+        self.Z, self.W, self.WW = [], [], []
+
+    def step(self) -> float:
+        z = np.asarray(self.P(self.r), dtype=np.float64).ravel().copy()
+        w = np.asarray(self.A(z), dtype=np.float64).ravel().copy()
+        for zj, wj, wwj in zip(self.Z, self.W, self.WW):
             beta = np.dot(w, wj) / wwj
             w -= beta * wj
             z -= beta * zj
         ww = np.dot(w, w)
         if not np.isfinite(ww) or ww == 0.0:
             raise FloatingPointError("GCR breakdown: <w, w> = %r" % ww)
-        alpha = np.dot(r, w) / ww
-        x += alpha * z
-        r -= alpha * w
+        alpha = np.dot(self.r, w) / ww
+        self.x += alpha * z
+        self.r -= alpha * w
+        if len(self.Z) + 1 >= self.restart:
+            self.Z, self.W, self.WW = [], [], []
+        else:
+            self.Z.append(z)
+            self.W.append(w)
+            self.WW.append(ww)
+        return np.linalg.norm(self.r) / self.nb
+
+
+def gcr(A: Callable, b: np.ndarray, P: Callable | None = None, tol: float = 1e-8,
+        restart: int = 5, maxiter: int = 500):
+    """Solve A x = b; returns (x, iterations, relative residual history)."""
+    g = GCR(A, b, P, restart)
+    hist = [1.0]
+    if g.nb == 0.0:
+        return g.x, 0, hist
+    it = 0
+    while it < maxiter:
+        hist.append(g.step())
         it += 1
-        hist.append(np.linalg.norm(r) / nb)
         if hist[-1] <= tol:
             break
-        if len(Z) + 1 >= restart:
-            Z, W, WW = [], [], []
-        else:
-            Z.append(z)
-            W.append(w)
-            WW.append(ww)
-    return x, it, hist
+    return g.x, it, hist

@@ -48,8 +48,8 @@ class _Mixed(ctypes.Structure):
 
 
 class _KRec(ctypes.Structure):
-    _fields_ = [("kind", ctypes.c_int32), ("level", ctypes.c_int32), ("bytes", ctypes.c_double),
-                ("ms", ctypes.c_double)]
+    _fields_ = [("kind", ctypes.c_int32), ("level", ctypes.c_int32), ("variant", ctypes.c_int32),
+                ("bytes", ctypes.c_double), ("ms", ctypes.c_double)]
 
 
 KERNEL_KINDS = ("sweep", "restrict", "prolong", "apply", "convert", "dot", "gcr_dots", "gcr_orth",
@@ -318,4 +318,5 @@ def mg_profile_stop(h: Handle) -> list[dict]:
     recs = (_KRec * cap)()
     cnt = ctypes.c_int32()
     _check(load().mg_profile_stop(h.ptr, recs, cap, ctypes.byref(cnt)), "mg_profile_stop")
-    return [dict(kind=KERNEL_KINDS[r.kind], level=r.level, bytes=r.bytes, ms=r.ms) for r in recs[:min(cnt.value, cap)]]
+    return [dict(kind=KERNEL_KINDS[r.kind], level=r.level, variant=r.variant, bytes=r.bytes, ms=r.ms)
+            for r in recs[:min(cnt.value, cap)]]

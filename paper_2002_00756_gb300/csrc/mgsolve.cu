@@ -89,7 +89,7 @@ struct mg_handle {
     std::vector<void*> allocs;
     // per-launch event profiling (mg_profile_start / mg_profile_stop)
     struct Rec {
-        int kind, level;
+        int kind, level, variant;
         double bytes;
     };
     bool prof = false;
@@ -163,10 +163,10 @@ struct Prof {
     mg_handle* h;
     cudaStream_t s;
     int idx = -1;
-    Prof(mg_handle* h_, int kind, int level, double bytes, cudaStream_t s_) : h(h_), s(s_) {
+    Prof(mg_handle* h_, int kind, int level, double bytes, cudaStream_t s_, int variant = 0) : h(h_), s(s_) {
         if (h && h->prof && 2 * (h->recs.size() + 1) <= h->evpool.size()) {
             idx = (int)h->recs.size();
-            h->recs.push_back({kind, level, bytes});
+            h->recs.push_back({kind, level, variant, bytes});
             cudaEventRecord(h->evpool[2 * idx], s);
         }
     }
@@ -249,7 +249,7 @@ mg_status launch_sweep(mg_handle* h, int lev, const Lvl<T, C>& L, const X* x, co
     if (MODE == mg::XM_PLAIN || MODE == mg::XM_PROLONG) per += sizeof(X);
     if (MODE == mg::XM_PROLONG || MODE == mg::XM_PROLONG0) per += 0.25 * sizeof(T);
     if (BCOPY) per += sizeof(T);
-    Prof pr(h, MG_K_SWEEP, lev, nc * per, s);
+    Prof pr(h, MG_K_SWEEP, lev, nc * per, s, MODE);
     // two threads per column; per thread the shared memory holds the asynchronous-copy
     // ring (DEEP slots of b, the next iterate and, unless BF16, three coefficients) and the
     // stash (2 values per step of half a column); it must fit the budget
@@ -939,6 +939,7 @@ mg_status mg_profile_stop(mg_handle* h, mg_kernel_record* out, int32_t cap, int3
         CK(cudaEventElapsedTime(&ms, h->evpool[2 * i], h->evpool[2 * i + 1]));
         out[i].kind = h->recs[i].kind;
         out[i].level = h->recs[i].level;
+        out[i].variant = h->recs[i].variant;
         out[i].bytes = h->recs[i].bytes;
         out[i].ms = ms;
     }
