@@ -42,14 +42,16 @@ WORKLOAD = "C192L70 pressure solve: GCR(5) FP64 outer + 4-level FP32 V-cycle, to
 SWEEP_VARIANTS = ("plain", "zero", "prolong", "prolong0")
 
 
+KERNEL_SOURCES = ("kernels.cuh", "krylov.cuh")   # all device code of the library
+
+
 def _source_digest() -> str:
-    """sha256 of the kernel sources: a committed ncu record is used only while it matches."""
+    """sha256 of the device-code sources: a committed ncu record is used only while it matches."""
     import hashlib
     hsh = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2002_00756_gb300", "csrc")
-    for f in sorted(os.listdir(csrc)):
-        if f.endswith((".cu", ".cuh", ".h", ".cpp")):
-            hsh.update(open(os.path.join(csrc, f), "rb").read())
+    for f in KERNEL_SOURCES:
+        hsh.update(open(os.path.join(csrc, f), "rb").read())
     return hsh.hexdigest()
 
 
@@ -204,6 +206,9 @@ def main():
     ap.add_argument("--precision", default="fp32", choices=["fp64", "fp32", "fp32_bf16"])
     ap.add_argument("--tol", type=float, default=1e-8)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile-solve", action="store_true",
+                    help="untimed: one pressure solve limited to --iters GCR iterations (for ncu captures)")
+    ap.add_argument("--iters", type=int, default=2)
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3
@@ -227,6 +232,14 @@ def main():
         pg.barrier()
     import paper_2002_00756_gb300 as mg
 
+    if args.profile_solve:
+        h = mg.mg_setup_config(cfg, inp, precision=args.precision, mixed=False, max_iter=args.iters)
+        b = torch.from_numpy(inp["rhs"]).cuda()
+        info = mg.pressure_solve(h, b, torch.zeros_like(b), tol=args.tol)
+        torch.cuda.synchronize()
+        print(json.dumps({"profile_solve": args.workload, "iters": info.iters, "rel_res": info.rel_res}))
+        h.destroy()
+        return
     h = mg.mg_setup_config(cfg, inp, precision=args.precision, mixed=False)
     stream = torch.cuda.current_stream()
     b = torch.from_numpy(inp["rhs"]).cuda()
@@ -293,9 +306,21 @@ def main():
             a[2] += r["bytes"]
     # the dominant kernel: the single kernel (kind, level, variant) with the most time
     (kind, lev, var), (cnt, ms, byt) = max(byv.items(), key=lambda kv: kv[1][1])
-    kname = f"{kind}@L{lev}" + (f"/{SWEEP_VARIANTS[var]}" if kind == "sweep" else "")
+    kname = f"{kind}@L{lev}" + (f"/{SWEEP_VARIANTS[var]}" if kind == "sweep" else
+                                (f"/J{var}" if kind == "apply" else ""))
     achieved = byt / (ms * 1e-3) / 1e9
     traffic = profiled_traffic(kname, cfg.name, args.precision)
+    roof = {"bound": "hbm", "kernel": kname, "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+            "frac": round(achieved / peak, 4)}
+    if kind == "apply":
+        # the fused FP64 apply issues 15 FP64 instructions per cell for H z plus J + 2 for the
+        # GCR sums; the bound is the FP64 issue rate: 152 SMs x 2 per clock x 2.07 GHz
+        fp64_peak = 152 * 2 * 2.07                      # G FP64 instructions / s
+        inst = (15 + var + 2) * cfg.ncell * cnt
+        ach = inst / (ms * 1e-3) / 1e9
+        roof = {"bound": "alu", "kernel": kname, "achieved": round(ach, 1), "peak": round(fp64_peak, 1),
+                "unit": "G FP64 inst/s", "frac": round(ach / fp64_peak, 4), "hbm_GBps": round(achieved, 1),
+                "hbm_frac": round(achieved / peak, 4)}
     vc_kinds = ("sweep", "restrict", "prolong", "convert")
     vc_ms = sum(v[1] for k, v in by.items() if k[0] in vc_kinds)
     vc_bytes = sum(v[2] for k, v in by.items() if k[0] in vc_kinds)
@@ -318,10 +343,9 @@ def main():
                    "l2": "working set (~3 GB) larger than L2; no flush"},
         "e2e": {"value": round(e2e_ms, 4), "unit": UNIT, "h2d_bytes_per_step": int(b.numel() * 8),
                 "d2h_bytes_per_step": int(b.numel() * 8)},
-        "roofline": {"bound": "hbm", "kernel": kname, "achieved": round(achieved, 1), "peak": peak,
-                     "unit": "GB/s", "frac": round(achieved / peak, 4),
-                     "traffic": None if traffic is None else round(traffic / 1e9 / (ms / cnt * 1e-3), 1),
-                     "traffic_bytes_per_launch": traffic, "algorithmic_bytes_per_launch": round(byt / cnt),
+        "roofline": {**roof,
+                     "traffic": traffic,
+                     "traffic_unit": "DRAM bytes per launch (ncu)", "algorithmic_bytes_per_launch": round(byt / cnt),
                      "launch_us": round(ms / cnt * 1e3, 2), "peak_source": peak_src + " (MEASURED_PEAKS.json hbm_gbs)",
                      "vcycle_GBps": round(vc_bytes / (vc_ms * 1e-3) / 1e9, 1),
                      "vcycle_frac": round(vc_bytes / (vc_ms * 1e-3) / 1e9 / peak, 4)},

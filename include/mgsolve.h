@@ -227,7 +227,8 @@ enum {
 typedef struct {
     int32_t kind;      /* MG_K_* */
     int32_t level;     /* multigrid level (0 = finest) */
-    int32_t variant;   /* sweeps: iterate source, 0 plain, 1 zero, 2 prolongated, 3 prolongation only */
+    int32_t variant;   /* sweeps: iterate source, 0 plain, 1 zero, 2 prolongated, 3 prolongation only;
+                          fused GCR apply: number of stored directions J; otherwise 0 */
     double bytes;      /* algorithmic bytes of the launch */
     double ms;         /* event-timed duration */
 } mg_kernel_record;

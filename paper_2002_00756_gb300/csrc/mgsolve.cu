@@ -436,7 +436,7 @@ struct RunApplyGcr {
     static mg_status run(mg_handle* h, const double* z, double* w, cudaStream_t s) {
         const Lvl<double, double> L = View<double, double>::lvl(h, 0);
         const double nc = (double)L.nlev * L.ncol;
-        Prof pr(h, MG_K_APPLY, 0, nc * 8.0 * (1 + 3 + 1 + 1 + J), s);   // z, 3 coefficients, w, r, w_i
+        Prof pr(h, MG_K_APPLY, 0, nc * 8.0 * (1 + 3 + 1 + 1 + J), s, J);   // z, 3 coefficients, w, r, w_i
         const int kc = GCR_APPLY_KCHUNK;
         dim3 grid((L.ncol + mg::RED_THREADS - 1) / mg::RED_THREADS, (L.nlev + kc - 1) / kc);
         mg::k_apply_gcr<J><<<grid, mg::RED_THREADS, 0, s>>>(L, z, w, h->W, h->glen, h->r, kc, h->partials,
