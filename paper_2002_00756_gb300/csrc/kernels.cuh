@@ -129,13 +129,16 @@ __global__ void __launch_bounds__(256) k_apply(Lvl<T, C> L, const X* __restrict_
 // Latency hiding: the streams first met in DRAM (the next iterate of the own column, b,
 // the E and N faces and the vertical face ahead) are copied DEEP steps ahead into a
 // per-thread shared-memory ring with asynchronous copies (cp.async via the CUDA pipeline
-// primitives), so they occupy no registers while in flight; loads that mostly hit in cache
-// (W and S faces, neighbour iterates, prolongation terms) run SHAL steps ahead in a
-// register ring, with 1/dz of the level.  Both rings are indexed statically: the step loop
-// is unrolled by DEEP.
+// primitives), so they occupy no registers while in flight.  The 16 lanes of a half-warp
+// hold 16 consecutive columns at the same level, so the E and W neighbour iterates are the
+// adjacent lanes' own values (warp shuffles) and the W face is the left lane's staged E face
+// (shared memory); only where a neighbour is not the adjacent column (ends of the 16-lane
+// group, panel edges) is it loaded.  Those loads, the N and S neighbours, the S face and the
+// prolongation terms run SHAL steps ahead in a register ring; 1/dz comes from a per-block
+// shared table.  Both rings are indexed statically: the step loop is unrolled by DEEP.
 template <typename T>
 struct SweepShal {
-    T xh[4], tw, ts, ch[4], cn, rdz;
+    T xh[4], tw, ts, ch[4], cn;
     T te, tn, tv;   // coefficients narrower than 4 bytes (BF16) travel here instead
 };
 
@@ -153,7 +156,7 @@ __global__ void k_sweep(Lvl<T, C> L, const X* __restrict__ x, const T* __restric
     const int nlev = L.nlev, hsteps = (nlev + 1) >> 1;
     const int tid = threadIdx.x, bd = blockDim.x;
     // shared memory: [ring of DEEP slots of b (B), xn (T), te, tn, tv (C, when staged)]
-    // [stash 2 x hsteps (T)]
+    // [stash 2 x hsteps (T)] [1/dz, nlev (T)]
     B* rb = reinterpret_cast<B*>(smem_raw);
     T* rx = reinterpret_cast<T*>(rb + (size_t)DEEP * bd);
     C* rte = reinterpret_cast<C*>(rx + (size_t)DEEP * bd);
@@ -162,6 +165,9 @@ __global__ void k_sweep(Lvl<T, C> L, const X* __restrict__ x, const T* __restric
     T* sc = reinterpret_cast<T*>(ASYNC_C ? (unsigned char*)(rtv + (size_t)DEEP * bd)
                                          : (unsigned char*)rte);
     T* se = sc + (size_t)hsteps * bd;
+    T* srdz = se + (size_t)hsteps * bd;   // [nlev]
+    for (int k = threadIdx.x; k < nlev; k += bd) srdz[k] = __ldg(L.rdz + k);
+    __syncthreads();
     const int lane = threadIdx.x & 31;
     const bool upper = lane >= 16;
     const int c_raw = blockIdx.x * (bd >> 1) + (threadIdx.x >> 5) * 16 + (lane & 15);
@@ -183,6 +189,12 @@ __global__ void k_sweep(Lvl<T, C> L, const X* __restrict__ x, const T* __restric
         for (int s = 0; s < 4; ++s) pn[s] = parent_col(nb[s], L.n);
     }
     const T rA = __ldg(L.rA + c);
+    // E / W neighbours that are the adjacent lanes of the 16-lane group
+    const int g = lane & 15;
+    const bool shE = g != 15 && nb[0] == c + 1;
+    const bool shW = g != 0 && nb[1] == c - 1;
+    // the W face is the left lane's E face when it is the same face
+    const bool shWf = ASYNC_C && shW && fo[1] == __ldg(L.fof + (c > 0 ? c - 1 : 0));
 
     // step i works on level kfirst + dir * i; the vertical face towards the next level in
     // the walk is Tv[k+1] going up and Tv[k] going down
@@ -210,18 +222,21 @@ __global__ void k_sweep(Lvl<T, C> L, const X* __restrict__ x, const T* __restric
         const size_t o = (size_t)k * ncol, oc = (size_t)k * ncol_c;
         const C* th = L.Th + (size_t)k * nf;
         if (RAW) {
-#pragma unroll
-            for (int s = 0; s < 4; ++s) d.xh[s] = ldx<T>(x + o + nb[s]);
+            if (!shE) d.xh[0] = ldx<T>(x + o + nb[0]);
+            if (!shW) d.xh[1] = ldx<T>(x + o + nb[1]);
+            d.xh[2] = ldx<T>(x + o + nb[2]);
+            d.xh[3] = ldx<T>(x + o + nb[3]);
         }
         if (PRO) {
-#pragma unroll
-            for (int s = 0; s < 4; ++s) d.ch[s] = __ldg(xc + oc + pn[s]);
+            if (!shE) d.ch[0] = __ldg(xc + oc + pn[0]);
+            if (!shW) d.ch[1] = __ldg(xc + oc + pn[1]);
+            d.ch[2] = __ldg(xc + oc + pn[2]);
+            d.ch[3] = __ldg(xc + oc + pn[3]);
             const int kn = k + dir;
             d.cn = (kn >= 0 && kn < nlev) ? __ldg(xc + (size_t)kn * ncol_c + pc) : T(0);
         }
-        d.tw = ldc<T>(th + fo[1]);
+        if (!shWf) d.tw = ldc<T>(th + fo[1]);
         d.ts = ldc<T>(th + fo[3]);
-        d.rdz = __ldg(L.rdz + k);
         if (!ASYNC_C) {
             d.te = ldc<T>(th + fo[0]);
             d.tn = ldc<T>(th + fo[2]);
@@ -244,16 +259,22 @@ __global__ void k_sweep(Lvl<T, C> L, const X* __restrict__ x, const T* __restric
         for (int j = 0; j < DEEP; ++j) {
             const int i = i0 + j;
             __pipeline_wait_prior(DEEP - 1);
+            __syncwarp();   // every lane's copies of this slot are complete and visible
             const size_t so = (size_t)j * bd + tid;
             const T bk = (T)rb[so];
             T xn = RAW ? rx[so] : T(0);
-            T te = T(0), tn = T(0), tv = T(0);
+            T te = T(0), tn = T(0), tv = T(0), twl = T(0);
             if (ASYNC_C) {
                 te = (T)rte[so];
                 tn = (T)rtn[so];
                 tv = (T)rtv[so];
+                if (shWf) twl = (T)rte[so - 1];
             }
+            __syncwarp();   // reads of the slot are done before it is refilled
             stage(i + DEEP, j);
+            // neighbour iterates at this level from the adjacent lanes (all lanes take part)
+            const T xEl = __shfl_down_sync(0xffffffffu, x0, 1);
+            const T xWl = __shfl_up_sync(0xffffffffu, x0, 1);
             if (i < nsteps) {
                 const SweepShal<T> e = sr[j % SHAL];
                 if (!ASYNC_C) {
@@ -273,19 +294,22 @@ __global__ void k_sweep(Lvl<T, C> L, const X* __restrict__ x, const T* __restric
 #pragma unroll
                     for (int s = 0; s < 4; ++s) xh[s] += e.ch[s];
                 }
-                const T rdz = e.rdz;
+                if (shE) xh[0] = xEl;
+                if (shW) xh[1] = xWl;
+                const T tw = shWf ? twl : e.tw;
+                const T rdz = srdz[k];
                 if (BCOPY) bcopy[(size_t)k * ncol + c] = bk;
                 T r = bk;
                 if (MODE != XM_ZERO) {
                     T hx = te * (x0 - xh[0]);
-                    hx += e.tw * (x0 - xh[1]);
+                    hx += tw * (x0 - xh[1]);
                     hx += tn * (x0 - xh[2]);
                     hx += e.ts * (x0 - xh[3]);
                     r -= x0 + (rA * hx + rdz * (tv * (x0 - xn) + tprev * (x0 - xprev)));
                 }
                 anext = rdz * tv;
                 const T m = (rdz * tprev) * ip;
-                q = (T(1) + rA * ((te + e.tw) + (tn + e.ts))) + m * q;
+                q = (T(1) + rA * ((te + tw) + (tn + e.ts))) + m * q;
                 const T p = q + anext;
                 y = r + m * y;
                 ip = T(1) / p;

@@ -257,11 +257,12 @@ mg_status launch_sweep(mg_handle* h, int lev, const Lvl<T, C>& L, const X* x, co
     const int hsteps = (L.nlev + 1) / 2;
     const size_t per_thread = DEEP * (sizeof(B) + sizeof(T) + (sizeof(C) >= 4 ? 3 * sizeof(C) : 0)) +
                               2 * (size_t)hsteps * sizeof(T);
+    const size_t per_block = (size_t)L.nlev * sizeof(T);   // the 1/dz table
     int bd = sweep_block(2 * L.ncol);
-    const int cap = (int)(SWEEP_SMEM_MAX / per_thread) / 32 * 32;
+    const int cap = (int)((SWEEP_SMEM_MAX - per_block) / per_thread) / 32 * 32;
     if (cap < 32) return MG_ERR_UNSUPPORTED;
     if (bd > cap) bd = cap;
-    const size_t smem = per_thread * bd;
+    const size_t smem = per_thread * bd + per_block;
     if (smem > 48 * 1024)
         CK(cudaFuncSetAttribute(mg::k_sweep<T, C, MODE, X, B, O, BCOPY, SweepPF<T>::deep, SweepPF<T>::shal>,
                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
