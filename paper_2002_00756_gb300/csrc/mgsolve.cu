@@ -241,6 +241,10 @@ struct SweepPF {
     static constexpr int shal = sizeof(T) == 8 ? 2 : MG_SWEEP_SHAL32;
 };
 
+#ifndef MG_SWEEP_IMPL
+#define MG_SWEEP_IMPL 1   // 1: block-cooperative three-phase sweep, 0: per-thread column walk
+#endif
+
 template <typename T, typename C, int MODE, typename X, typename B, typename O, bool BCOPY>
 mg_status launch_sweep(mg_handle* h, int lev, const Lvl<T, C>& L, const X* x, const T* xc, int ncol_c,
                        const B* b, T* bcopy, O* xo, double omega, cudaStream_t s) {
@@ -250,6 +254,29 @@ mg_status launch_sweep(mg_handle* h, int lev, const Lvl<T, C>& L, const X* x, co
     if (MODE == mg::XM_PROLONG || MODE == mg::XM_PROLONG0) per += 0.25 * sizeof(T);
     if (BCOPY) per += sizeof(T);
     Prof pr(h, MG_K_SWEEP, lev, nc * per, s, MODE);
+    if (MG_SWEEP_IMPL == 1) {
+        // tiles of 32 columns (16 on small levels, to spread them over the SMs)
+        const size_t cell = 5 * sizeof(T);
+        if (L.ncol >= 32 * 600) {
+            constexpr int TC = 32;
+            const size_t smem = cell * L.nlev * TC;
+            if (smem > 48 * 1024)
+                CK(cudaFuncSetAttribute(mg::k_sweep_blk<T, C, MODE, X, B, O, BCOPY, TC>,
+                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+            mg::k_sweep_blk<T, C, MODE, X, B, O, BCOPY, TC>
+                <<<(L.ncol + TC - 1) / TC, 256, smem, s>>>(L, x, xc, ncol_c, b, bcopy, xo, (T)omega);
+        } else {
+            constexpr int TC = 16;
+            const size_t smem = cell * L.nlev * TC;
+            if (smem > 48 * 1024)
+                CK(cudaFuncSetAttribute(mg::k_sweep_blk<T, C, MODE, X, B, O, BCOPY, TC>,
+                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+            mg::k_sweep_blk<T, C, MODE, X, B, O, BCOPY, TC>
+                <<<(L.ncol + TC - 1) / TC, 128, smem, s>>>(L, x, xc, ncol_c, b, bcopy, xo, (T)omega);
+        }
+        CK(cudaGetLastError());
+        return MG_OK;
+    }
     // two threads per column; per thread the shared memory holds the asynchronous-copy
     // ring (DEEP slots of b, the next iterate and, unless BF16, three coefficients) and the
     // stash (2 values per step of half a column); it must fit the budget
