@@ -346,138 +346,6 @@ __global__ void k_sweep(Lvl<T, C> L, const X* __restrict__ x, const T* __restric
 }
 
 // ---------------------------------------------------------------------------------------
-// Block-Jacobi sweep, block-cooperative form: a block owns TC consecutive columns and runs
-// three phases through shared memory.
-//  1. every (level, column) cell of the tile, in parallel over the block's threads (one warp
-//     row per level, columns fastest, so loads are coalesced and independent): residual
-//     r = b - H x, row excess s = 1 + horizontal coefficients, couplings a_up, a_dn and the
-//     iterate x;
-//  2. two threads per column solve the column system from both ends (the twisted
-//     elimination described above k_sweep) out of shared memory, back-substituting the
-//     output recurrence out_i = w_i + e_i out_{i+1} in place;
-//  3. the block writes the tile of x_out, coalesced.
-// Memory access (phases 1 and 3) never waits on the vertical recurrence (phase 2), and the
-// recurrence never waits on memory.  Shared memory: 5 values per cell of the tile.
-template <typename T, typename C, int MODE, typename X, typename B, typename O, bool BCOPY, int TC>
-__global__ void k_sweep_blk(Lvl<T, C> L, const X* __restrict__ x, const T* __restrict__ xc,
-                            int ncol_c, const B* __restrict__ b, T* __restrict__ bcopy,
-                            O* __restrict__ xo, T omega) {
-    constexpr bool PRO = (MODE == XM_PROLONG || MODE == XM_PROLONG0);
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int nlev = L.nlev;
-    const size_t cells = (size_t)nlev * TC;
-    T* R = reinterpret_cast<T*>(smem_raw);   // residual, then w_i, then out
-    T* Sx = R + cells;                         // row excess, then e_i
-    T* AU = Sx + cells;                        // coupling to the level above
-    T* AD = AU + cells;                        // coupling to the level below
-    T* X0 = AD + cells;                        // iterate
-    const size_t ncol = L.ncol, nf = 2 * ncol;
-    const int c0 = blockIdx.x * TC;
-    const int nthr = blockDim.x;
-
-    // ---- phase 1 ----
-    for (int e = threadIdx.x; e < nlev * TC; e += nthr) {
-        const int k = e / TC, j = e - k * TC;
-        const int c = min(c0 + j, L.ncol - 1);
-        const size_t o = (size_t)k * ncol;
-        int nb[4], fo[4];
-#pragma unroll
-        for (int s = 0; s < 4; ++s) {
-            nb[s] = __ldg(L.nbr + s * ncol + c);
-            fo[s] = __ldg(L.fof + s * ncol + c);
-        }
-        const C* th = L.Th + (size_t)k * nf;
-        const T te = ldc<T>(th + fo[0]), tw = ldc<T>(th + fo[1]);
-        const T tn = ldc<T>(th + fo[2]), ts = ldc<T>(th + fo[3]);
-        const T tup = ldc<T>(L.Tv + o + ncol + c), tdn = ldc<T>(L.Tv + o + c);
-        const T rdz = __ldg(L.rdz + k), rA = __ldg(L.rA + c);
-        const T bk = (T)__ldg(b + o + c);
-        if (BCOPY && c0 + j < L.ncol) bcopy[o + c] = bk;
-        T x0 = T(0), r = bk;
-        if (MODE != XM_ZERO) {
-            const size_t oc = (size_t)k * ncol_c;
-            const int pc = PRO ? parent_col(c, L.n) : 0;
-            x0 = xval<MODE, T>(x, xc, o, oc, c, pc);
-            const T xu = (k + 1 < nlev) ? xval<MODE, T>(x, xc, o + ncol, oc + ncol_c, c, pc) : T(0);
-            const T xd = (k > 0) ? xval<MODE, T>(x, xc, o - ncol, oc - ncol_c, c, pc) : T(0);
-            T xn[4];
-#pragma unroll
-            for (int s = 0; s < 4; ++s) xn[s] = xval<MODE, T>(x, xc, o, oc, nb[s], PRO ? parent_col(nb[s], L.n) : 0);
-            T hx = te * (x0 - xn[0]);
-            hx += tw * (x0 - xn[1]);
-            hx += tn * (x0 - xn[2]);
-            hx += ts * (x0 - xn[3]);
-            r -= x0 + (rA * hx + rdz * (tup * (x0 - xu) + tdn * (x0 - xd)));
-        }
-        R[e] = r;
-        Sx[e] = T(1) + rA * ((te + tw) + (tn + ts));
-        AU[e] = rdz * tup;
-        AD[e] = rdz * tdn;
-        X0[e] = x0;
-    }
-    __syncthreads();
-
-    // ---- phase 2: threads 0..TC-1 take the lower halves, TC..2TC-1 the upper halves ----
-    const int hsteps = (nlev + 1) >> 1;
-    const bool solver = threadIdx.x < 2 * TC;
-    const bool upper = threadIdx.x >= TC;
-    const int j = threadIdx.x - (upper ? TC : 0);
-    const int nsteps = upper ? nlev - hsteps : hsteps;
-    const int dir = upper ? -1 : 1, kfirst = upper ? nlev - 1 : 0;
-    T q = T(0), ip = T(0), y = T(0), anext = T(0), xlast = T(0);
-    __shared__ T xch[3][2 * TC];
-    if (solver) {
-        for (int i = 0; i < nsteps; ++i) {
-            const int k = kfirst + dir * i;
-            const int e = k * TC + j;
-            const T r = R[e], sk = Sx[e], x0 = X0[e];
-            const T aprev = upper ? AU[e] : AD[e];
-            anext = upper ? AD[e] : AU[e];
-            const T m = aprev * ip;
-            q = sk + m * q;
-            const T p = q + anext;
-            y = r + m * y;
-            ip = T(1) / p;
-            const T ei = anext * ip;
-            const int kn = k + dir;
-            const T xnext = (kn >= 0 && kn < nlev) ? X0[kn * TC + j] : T(0);
-            R[e] = x0 + omega * (y * ip) - ei * xnext;
-            Sx[e] = ei;
-            xlast = x0;
-        }
-        xch[0][threadIdx.x] = q;
-        xch[1][threadIdx.x] = y;
-        xch[2][threadIdx.x] = anext;
-    }
-    __syncthreads();
-    if (solver && nsteps > 0) {
-        T dlt;
-        if (nlev - hsteps == 0) {
-            dlt = y * ip;
-        } else {
-            const int o = upper ? threadIdx.x - TC : threadIdx.x + TC;
-            const T qo = xch[0][o], yo = xch[1][o], ao = xch[2][o];
-            const T po = qo + ao;
-            dlt = (y * po + anext * yo) / (q * po + anext * qo);
-        }
-        T out = xlast + omega * dlt;
-        R[(kfirst + dir * (nsteps - 1)) * TC + j] = out;
-        for (int i = nsteps - 2; i >= 0; --i) {
-            const int e = (kfirst + dir * i) * TC + j;
-            out = R[e] + Sx[e] * out;
-            R[e] = out;
-        }
-    }
-    __syncthreads();
-
-    // ---- phase 3 ----
-    for (int e = threadIdx.x; e < nlev * TC; e += nthr) {
-        const int k = e / TC, jj = e - k * TC;
-        if (c0 + jj < L.ncol) xo[(size_t)k * ncol + c0 + jj] = (O)R[e];
-    }
-}
-
-// ---------------------------------------------------------------------------------------
 // Residual and restriction (Algorithm 1): bc[k][C] = sum_q w[q][C] (b - H x)[k][child_q],
 // w = area_child / area_C; one thread per coarse column and chunk of kchunk levels (there is
 // no vertical recurrence, so short chunks give many independent threads).
@@ -535,8 +403,9 @@ __global__ void __launch_bounds__(128) k_resid_restrict(Lvl<T, C> L, const X* __
 
 // Residual and restriction, one thread per fine column (for n divisible by 16): a warp
 // covers fine columns i0..i0+15 of rows 2J (lanes 0-15) and 2J+1 (lanes 16-31) of one
-// panel, i.e. 8 coarse columns; the 2x2 sums of w_child r_child are two shuffles.  Each
-// thread walks kchunk levels with loads issued SHAL levels ahead in a register ring.
+// panel, i.e. 8 coarse columns; the 2x2 sums of w_child r_child are two shuffles, and the
+// E / W neighbour iterates and the W face come from the adjacent lanes.  Each thread walks
+// kchunk levels with loads issued SHAL levels ahead in a register ring.
 template <typename T, typename C, bool XZERO, typename X, typename B, typename O, int SHAL>
 __global__ void __launch_bounds__(128) k_resid_restrict16(Lvl<T, C> L, const X* __restrict__ x,
                                                            const B* __restrict__ b,
@@ -564,6 +433,12 @@ __global__ void __launch_bounds__(128) k_resid_restrict16(Lvl<T, C> L, const X* 
     }
     const T rA = __ldg(L.rA + c);
     const T wc = __ldg(w + (size_t)q * ncol_c + Cc);
+    // E / W neighbours that are the adjacent lanes of the 16-lane row group: their iterate
+    // and (W) face coefficient come by shuffle instead of a load
+    const int gl = lane & 15;
+    const bool shE = gl != 15 && nb[0] == c + 1;
+    const bool shW = gl != 0 && nb[1] == c - 1;
+    const bool shWf = shW && fo[1] == __ldg(L.fof + (c > 0 ? c - 1 : 0));
     struct Lv {
         T xp, xn[4], b, th[4], tup, rdz;
     };
@@ -571,12 +446,16 @@ __global__ void __launch_bounds__(128) k_resid_restrict16(Lvl<T, C> L, const X* 
         const size_t o = (size_t)k * ncol;
         if (!XZERO) {
             d.xp = (k + 1 < L.nlev) ? ldx<T>(x + o + ncol + c) : T(0);
-#pragma unroll
-            for (int s = 0; s < 4; ++s) d.xn[s] = ldx<T>(x + o + nb[s]);
+            if (!shE) d.xn[0] = ldx<T>(x + o + nb[0]);
+            if (!shW) d.xn[1] = ldx<T>(x + o + nb[1]);
+            d.xn[2] = ldx<T>(x + o + nb[2]);
+            d.xn[3] = ldx<T>(x + o + nb[3]);
         }
         const C* th = L.Th + (size_t)k * nf;
-#pragma unroll
-        for (int s = 0; s < 4; ++s) d.th[s] = ldc<T>(th + fo[s]);
+        d.th[0] = ldc<T>(th + fo[0]);
+        if (!shWf) d.th[1] = ldc<T>(th + fo[1]);
+        d.th[2] = ldc<T>(th + fo[2]);
+        d.th[3] = ldc<T>(th + fo[3]);
         d.tup = ldc<T>(L.Tv + o + ncol + c);
         d.b = (T)__ldg(b + o + c);
         d.rdz = __ldg(L.rdz + k);
@@ -595,10 +474,16 @@ __global__ void __launch_bounds__(128) k_resid_restrict16(Lvl<T, C> L, const X* 
             if (k < k1) {
                 const Lv d = ring[j];
                 if (k + SHAL < k1) load(k + SHAL, ring[j]);
+                const T twl = __shfl_up_sync(0xffffffffu, d.th[0], 1);
+                const T xEl = __shfl_down_sync(0xffffffffu, x0, 1);
+                const T xWl = __shfl_up_sync(0xffffffffu, x0, 1);
+                const T tw = shWf ? twl : d.th[1];
                 T r = d.b;
                 if (!XZERO) {
-                    T h = d.th[0] * (x0 - d.xn[0]);
-                    h += d.th[1] * (x0 - d.xn[1]);
+                    const T xE = shE ? xEl : d.xn[0];
+                    const T xW = shW ? xWl : d.xn[1];
+                    T h = d.th[0] * (x0 - xE);
+                    h += tw * (x0 - xW);
                     h += d.th[2] * (x0 - d.xn[2]);
                     h += d.th[3] * (x0 - d.xn[3]);
                     r -= x0 + (rA * h + d.rdz * (d.tup * (x0 - d.xp) + tdn * (x0 - xm)));

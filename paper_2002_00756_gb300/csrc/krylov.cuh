@@ -277,45 +277,43 @@ __global__ void k_mx_cells(MixedDev M, const double* __restrict__ uh, const doub
 
 // Pressure-system GCR pass 1: w = H z (FP64, Eq. helmholtz_operator) for the levels
 // [k0, k0 + kchunk) of one column per thread, fused with the GCR sums of the new direction J.
+// The finest level keeps its six couplings per cell premultiplied in FP64 (a6[side][k][c],
+// sides E, W, N, S, up, down), so H z costs 6 differences and 6 fused multiply-adds: FP64
+// issue, not memory, bounds this kernel on GB300.
 template <int J>
-__global__ void __launch_bounds__(RED_THREADS) k_apply_gcr(Lvl<double, double> L, const double* __restrict__ z,
-                                                           double* __restrict__ w, const double* __restrict__ Wb,
-                                                           size_t ld, const double* __restrict__ r, int kchunk,
+__global__ void __launch_bounds__(RED_THREADS) k_apply_gcr(Lvl<double, double> L, const double* __restrict__ a6,
+                                                           const double* __restrict__ z, double* __restrict__ w,
+                                                           const double* __restrict__ Wb, size_t ld,
+                                                           const double* __restrict__ r, int kchunk,
                                                            double* partials, unsigned int* ticket, GcrScal* S) {
     double v[J + 2], t[J + 2];
 #pragma unroll
     for (int i = 0; i < J + 2; ++i) v[i] = 0.0;
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
     if (c < L.ncol) {
-        const size_t ncol = L.ncol, nf = 2 * ncol;
+        const size_t ncol = L.ncol, N = (size_t)L.nlev * ncol;
         const int k0 = blockIdx.y * kchunk;
         const int k1 = min(L.nlev, k0 + kchunk);
-        int nb[4], fo[4];
+        int nb[4];
 #pragma unroll
-        for (int s = 0; s < 4; ++s) {
-            nb[s] = __ldg(L.nbr + s * ncol + c);
-            fo[s] = __ldg(L.fof + s * ncol + c);
-        }
-        const double rA = __ldg(L.rA + c);
+        for (int s = 0; s < 4; ++s) nb[s] = __ldg(L.nbr + s * ncol + c);
         double xm = k0 > 0 ? __ldg(z + (size_t)(k0 - 1) * ncol + c) : 0.0;
         double x0 = __ldg(z + (size_t)k0 * ncol + c);
-        double tdn = __ldg(L.Tv + (size_t)k0 * ncol + c);
 #pragma unroll 2
         for (int k = k0; k < k1; ++k) {
-            const size_t o = (size_t)k * ncol;
+            const size_t o = (size_t)k * ncol, e = o + c;
             const double xp = (k + 1 < L.nlev) ? __ldg(z + o + ncol + c) : 0.0;
-            const double tup = __ldg(L.Tv + o + ncol + c);
-            const double* th = L.Th + (size_t)k * nf;
-            double h = __ldg(th + fo[0]) * (x0 - __ldg(z + o + nb[0]));
-            h += __ldg(th + fo[1]) * (x0 - __ldg(z + o + nb[1]));
-            h += __ldg(th + fo[2]) * (x0 - __ldg(z + o + nb[2]));
-            h += __ldg(th + fo[3]) * (x0 - __ldg(z + o + nb[3]));
-            const double we = x0 + (rA * h + __ldg(L.rdz + k) * (tup * (x0 - xp) + tdn * (x0 - xm)));
-            w[o + c] = we;
-            gcr_accumulate<J>(v, we, __ldg(r + o + c), Wb, ld, o + c);
+            double we = x0;
+            we = fma(__ldg(a6 + e), x0 - __ldg(z + o + nb[0]), we);
+            we = fma(__ldg(a6 + N + e), x0 - __ldg(z + o + nb[1]), we);
+            we = fma(__ldg(a6 + 2 * N + e), x0 - __ldg(z + o + nb[2]), we);
+            we = fma(__ldg(a6 + 3 * N + e), x0 - __ldg(z + o + nb[3]), we);
+            we = fma(__ldg(a6 + 4 * N + e), x0 - xp, we);
+            we = fma(__ldg(a6 + 5 * N + e), x0 - xm, we);
+            w[e] = we;
+            gcr_accumulate<J>(v, we, __ldg(r + e), Wb, ld, e);
             xm = x0;
             x0 = xp;
-            tdn = tup;
         }
     }
     if (grid_reduce<J + 2>(v, partials, ticket, t)) gcr_coeffs<J>(t, S);

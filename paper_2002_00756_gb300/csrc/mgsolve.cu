@@ -67,6 +67,7 @@ struct mg_handle {
     std::vector<DevLevel> lv;
     double* rdz64 = nullptr;
     float* rdz32 = nullptr;
+    double* a6 = nullptr;       // finest level: six premultiplied FP64 couplings per cell
     // GCR
     size_t glen = 0;            // length of a GCR vector (N, or nu + N with mixed data)
     double* Z = nullptr;        // [restart][glen]
@@ -241,10 +242,6 @@ struct SweepPF {
     static constexpr int shal = sizeof(T) == 8 ? 2 : MG_SWEEP_SHAL32;
 };
 
-#ifndef MG_SWEEP_IMPL
-#define MG_SWEEP_IMPL 1   // 1: block-cooperative three-phase sweep, 0: per-thread column walk
-#endif
-
 template <typename T, typename C, int MODE, typename X, typename B, typename O, bool BCOPY>
 mg_status launch_sweep(mg_handle* h, int lev, const Lvl<T, C>& L, const X* x, const T* xc, int ncol_c,
                        const B* b, T* bcopy, O* xo, double omega, cudaStream_t s) {
@@ -254,29 +251,6 @@ mg_status launch_sweep(mg_handle* h, int lev, const Lvl<T, C>& L, const X* x, co
     if (MODE == mg::XM_PROLONG || MODE == mg::XM_PROLONG0) per += 0.25 * sizeof(T);
     if (BCOPY) per += sizeof(T);
     Prof pr(h, MG_K_SWEEP, lev, nc * per, s, MODE);
-    if (MG_SWEEP_IMPL == 1) {
-        // tiles of 32 columns (16 on small levels, to spread them over the SMs)
-        const size_t cell = 5 * sizeof(T);
-        if (L.ncol >= 32 * 600) {
-            constexpr int TC = 32;
-            const size_t smem = cell * L.nlev * TC;
-            if (smem > 48 * 1024)
-                CK(cudaFuncSetAttribute(mg::k_sweep_blk<T, C, MODE, X, B, O, BCOPY, TC>,
-                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-            mg::k_sweep_blk<T, C, MODE, X, B, O, BCOPY, TC>
-                <<<(L.ncol + TC - 1) / TC, 256, smem, s>>>(L, x, xc, ncol_c, b, bcopy, xo, (T)omega);
-        } else {
-            constexpr int TC = 16;
-            const size_t smem = cell * L.nlev * TC;
-            if (smem > 48 * 1024)
-                CK(cudaFuncSetAttribute(mg::k_sweep_blk<T, C, MODE, X, B, O, BCOPY, TC>,
-                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-            mg::k_sweep_blk<T, C, MODE, X, B, O, BCOPY, TC>
-                <<<(L.ncol + TC - 1) / TC, 128, smem, s>>>(L, x, xc, ncol_c, b, bcopy, xo, (T)omega);
-        }
-        CK(cudaGetLastError());
-        return MG_OK;
-    }
     // two threads per column; per thread the shared memory holds the asynchronous-copy
     // ring (DEEP slots of b, the next iterate and, unless BF16, three coefficients) and the
     // stash (2 values per step of half a column); it must fit the budget
@@ -464,10 +438,10 @@ struct RunApplyGcr {
     static mg_status run(mg_handle* h, const double* z, double* w, cudaStream_t s) {
         const Lvl<double, double> L = View<double, double>::lvl(h, 0);
         const double nc = (double)L.nlev * L.ncol;
-        Prof pr(h, MG_K_APPLY, 0, nc * 8.0 * (1 + 3 + 1 + 1 + J), s, J);   // z, 3 coefficients, w, r, w_i
+        Prof pr(h, MG_K_APPLY, 0, nc * 8.0 * (1 + 6 + 1 + 1 + J), s, J);   // z, 6 couplings, w, r, w_i
         const int kc = GCR_APPLY_KCHUNK;
         dim3 grid((L.ncol + mg::RED_THREADS - 1) / mg::RED_THREADS, (L.nlev + kc - 1) / kc);
-        mg::k_apply_gcr<J><<<grid, mg::RED_THREADS, 0, s>>>(L, z, w, h->W, h->glen, h->r, kc, h->partials,
+        mg::k_apply_gcr<J><<<grid, mg::RED_THREADS, 0, s>>>(L, h->a6, z, w, h->W, h->glen, h->r, kc, h->partials,
                                                             h->tickets + TK_SUMS, h->gs);
         CK(cudaGetLastError());
         return MG_OK;
@@ -700,6 +674,22 @@ mg_status setup_impl(mg_handle* h, const mg_mesh* mesh, const mg_params* prm, co
             TRY(upload(h, &d.w64, w));
             if (prec != MG_FP64) TRY(upload(h, &d.w32, w));
         }
+    }
+    {
+        // finest level: a_side = Th[k][face] / area, a_up = Tv[k+1] / dz, a_dn = Tv[k] / dz
+        const mg::HGeom& G = hg[0];
+        const size_t N = (size_t)nlev * ncol0;
+        std::vector<double> a6(6 * N);
+        for (int k = 0; k < nlev; ++k)
+            for (int c = 0; c < ncol0; ++c) {
+                const size_t e = (size_t)k * ncol0 + c;
+                const double rA = 1.0 / G.area[c];
+                for (int sd = 0; sd < 4; ++sd)
+                    a6[sd * N + e] = co[0].Th[(size_t)k * 2 * ncol0 + G.face_of[sd * ncol0 + c]] * rA;
+                a6[4 * N + e] = co[0].Tv[(size_t)(k + 1) * ncol0 + c] * rdz[k];
+                a6[5 * N + e] = co[0].Tv[(size_t)k * ncol0 + c] * rdz[k];
+            }
+        TRY(upload(h, &h->a6, a6));
     }
     // mixed system arrays (finest level)
     h->mixed = mixed != nullptr;
