@@ -36,15 +36,6 @@ __device__ __forceinline__ float ldc<float, __nv_bfloat16>(const __nv_bfloat16* 
     return __bfloat162float(__ldg(p));
 }
 
-template <typename T, typename C>
-__device__ __forceinline__ T ldc_val(C v) {
-    return (T)v;
-}
-template <>
-__device__ __forceinline__ float ldc_val<float, __nv_bfloat16>(__nv_bfloat16 v) {
-    return __bfloat162float(v);
-}
-
 template <typename T, typename X>
 __device__ __forceinline__ T ldx(const X* p) {
     return (T)__ldg(p);
@@ -155,18 +146,14 @@ struct SweepShal {
     T te, tn, tv;   // coefficients narrower than 4 bytes (BF16) travel here instead
 };
 
-template <typename T, typename C, int MODE, typename X, typename B, typename O, bool BCOPY, int DEEP, int SHAL,
-          bool STAGE>
+template <typename T, typename C, int MODE, typename X, typename B, typename O, bool BCOPY, int DEEP, int SHAL>
 __global__ void k_sweep(Lvl<T, C> L, const X* __restrict__ x, const T* __restrict__ xc,
                         int ncol_c, const B* __restrict__ b, T* __restrict__ bcopy,
                         O* __restrict__ xo, T omega) {
     static_assert(DEEP % SHAL == 0, "ring lengths");
     static_assert(sizeof(X) == sizeof(T), "iterate type");
-    // STAGE: the deep stream goes through the shared-memory ring; otherwise through a
-    // register ring.  Asynchronous copies move 4, 8 or 16 bytes: BF16 coefficients always
-    // use registers.
-    constexpr bool ASYNC_C = STAGE && sizeof(C) >= 4;
-    constexpr int RING = STAGE ? DEEP : 0;
+    // asynchronous copies move 4, 8 or 16 bytes: BF16 coefficients use the register ring
+    constexpr bool ASYNC_C = sizeof(C) >= 4;
     constexpr bool PRO = (MODE == XM_PROLONG || MODE == XM_PROLONG0);
     constexpr bool RAW = (MODE == XM_PLAIN || MODE == XM_PROLONG);   // reads the fine iterate
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -175,11 +162,11 @@ __global__ void k_sweep(Lvl<T, C> L, const X* __restrict__ x, const T* __restric
     // shared memory: [ring of DEEP slots of b (B), xn (T), te, tn, tv (C, when staged)]
     // [stash 2 x hsteps (T)] [1/dz, nlev (T)]
     B* rb = reinterpret_cast<B*>(smem_raw);
-    T* rx = reinterpret_cast<T*>(rb + (size_t)RING * bd);
-    C* rte = reinterpret_cast<C*>(rx + (size_t)RING * bd);
-    C* rtn = rte + (size_t)RING * bd;
-    C* rtv = rtn + (size_t)RING * bd;
-    T* sc = reinterpret_cast<T*>(ASYNC_C ? (unsigned char*)(rtv + (size_t)RING * bd)
+    T* rx = reinterpret_cast<T*>(rb + (size_t)DEEP * bd);
+    C* rte = reinterpret_cast<C*>(rx + (size_t)DEEP * bd);
+    C* rtn = rte + (size_t)DEEP * bd;
+    C* rtv = rtn + (size_t)DEEP * bd;
+    T* sc = reinterpret_cast<T*>(ASYNC_C ? (unsigned char*)(rtv + (size_t)DEEP * bd)
                                          : (unsigned char*)rte);
     T* se = sc + (size_t)hsteps * bd;
     T* srdz = se + (size_t)hsteps * bd;   // [nlev]
@@ -211,12 +198,11 @@ __global__ void k_sweep(Lvl<T, C> L, const X* __restrict__ x, const T* __restric
     const bool shE = g != 15 && nb[0] == c + 1;
     const bool shW = g != 0 && nb[1] == c - 1;
     // the W face is the left lane's E face when it is the same face
-    const bool shWf = (ASYNC_C || !STAGE) && shW && fo[1] == __ldg(L.fof + (c > 0 ? c - 1 : 0));
+    const bool shWf = ASYNC_C && shW && fo[1] == __ldg(L.fof + (c > 0 ? c - 1 : 0));
 
     // step i works on level kfirst + dir * i; the vertical face towards the next level in
     // the walk is Tv[k+1] going up and Tv[k] going down
     auto stage = [&](int i, int slot) {
-        if (!STAGE) return;
         if (i < nsteps) {
             const int k = kfirst + dir * i;
             const int kn = k + dir;
@@ -234,24 +220,6 @@ __global__ void k_sweep(Lvl<T, C> L, const X* __restrict__ x, const T* __restric
             }
         }
         __pipeline_commit();
-    };
-    struct Deep {
-        B b;
-        T xn;
-        C te, tn, tv;
-    };
-    auto load_deep = [&](int i, Deep& d) {
-        if (i < nsteps) {
-            const int k = kfirst + dir * i;
-            const int kn = k + dir;
-            const int o = k * ncol;
-            const C* th = L.Th + k * nf;
-            d.b = __ldg(b + o + c);
-            if (RAW) d.xn = (kn >= 0 && kn < nlev) ? ldx<T>(x + kn * ncol + c) : T(0);
-            d.te = __ldg(th + fo[0]);
-            d.tn = __ldg(th + fo[2]);
-            d.tv = __ldg(L.Tv + (upper ? k : k + 1) * ncol + c);
-        }
     };
     auto load_shal = [&](int i, SweepShal<T>& d) {
         const int k = kfirst + dir * i;
@@ -273,7 +241,7 @@ __global__ void k_sweep(Lvl<T, C> L, const X* __restrict__ x, const T* __restric
         }
         if (!shWf) d.tw = ldc<T>(th + fo[1]);
         d.ts = ldc<T>(th + fo[3]);
-        if (STAGE && !ASYNC_C) {
+        if (!ASYNC_C) {
             d.te = ldc<T>(th + fo[0]);
             d.tn = ldc<T>(th + fo[2]);
             d.tv = ldc<T>(L.Tv + (upper ? k : k + 1) * ncol + c);
@@ -282,11 +250,6 @@ __global__ void k_sweep(Lvl<T, C> L, const X* __restrict__ x, const T* __restric
 
 #pragma unroll
     for (int j = 0; j < DEEP; ++j) stage(j, j);
-    Deep dr[STAGE ? 1 : DEEP];
-    if (!STAGE) {
-#pragma unroll
-        for (int j = 0; j < DEEP; ++j) load_deep(j, dr[STAGE ? 0 : j]);
-    }
     SweepShal<T> sr[SHAL];
 #pragma unroll
     for (int j = 0; j < SHAL; ++j)
@@ -299,37 +262,26 @@ __global__ void k_sweep(Lvl<T, C> L, const X* __restrict__ x, const T* __restric
 #pragma unroll
         for (int j = 0; j < DEEP; ++j) {
             const int i = i0 + j;
-            T bk, xn = T(0), te = T(0), tn = T(0), tv = T(0), twl = T(0);
-            if (STAGE) {
-                __pipeline_wait_prior(DEEP - 1);
-                __syncwarp();   // every lane's copies of this slot are complete and visible
-                const int so = j * bd + tid;
-                bk = (T)rb[so];
-                if (RAW) xn = rx[so];
-                if (ASYNC_C) {
-                    te = (T)rte[so];
-                    tn = (T)rtn[so];
-                    tv = (T)rtv[so];
-                    if (shWf) twl = (T)rte[so - 1];
-                }
-                __syncwarp();   // reads of the slot are done before it is refilled
-                stage(i + DEEP, j);
-            } else {
-                const Deep d = dr[STAGE ? 0 : j];
-                load_deep(i + DEEP, dr[STAGE ? 0 : j]);
-                bk = (T)d.b;
-                if (RAW) xn = d.xn;
-                te = ldc_val<T>(d.te);
-                tn = ldc_val<T>(d.tn);
-                tv = ldc_val<T>(d.tv);
-                twl = __shfl_up_sync(0xffffffffu, te, 1);
+            __pipeline_wait_prior(DEEP - 1);
+            __syncwarp();   // every lane's copies of this slot are complete and visible
+            const int so = j * bd + tid;
+            const T bk = (T)rb[so];
+            T xn = RAW ? rx[so] : T(0);
+            T te = T(0), tn = T(0), tv = T(0), twl = T(0);
+            if (ASYNC_C) {
+                te = (T)rte[so];
+                tn = (T)rtn[so];
+                tv = (T)rtv[so];
+                if (shWf) twl = (T)rte[so - 1];
             }
+            __syncwarp();   // reads of the slot are done before it is refilled
+            stage(i + DEEP, j);
             // neighbour iterates at this level from the adjacent lanes (all lanes take part)
             const T xEl = __shfl_down_sync(0xffffffffu, x0, 1);
             const T xWl = __shfl_up_sync(0xffffffffu, x0, 1);
             if (i < nsteps) {
                 const SweepShal<T> e = sr[j % SHAL];
-                if (STAGE && !ASYNC_C) {
+                if (!ASYNC_C) {
                     te = e.te;
                     tn = e.tn;
                     tv = e.tv;
@@ -374,7 +326,7 @@ __global__ void k_sweep(Lvl<T, C> L, const X* __restrict__ x, const T* __restric
             }
         }
     }
-    if (STAGE) __pipeline_wait_prior(0);
+    __pipeline_wait_prior(0);
     // interface rows h-1 (lower half) and h (upper half)
     const T qo = __shfl_xor_sync(0xffffffffu, q, 16);
     const T yo = __shfl_xor_sync(0xffffffffu, y, 16);

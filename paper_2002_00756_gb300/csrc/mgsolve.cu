@@ -28,9 +28,6 @@
 #ifndef MG_SWEEP_BLOCK
 #define MG_SWEEP_BLOCK 128
 #endif
-#ifndef MG_SWEEP_STAGE
-#define MG_SWEEP_STAGE 1   // deep prefetch through shared memory (1) or registers (0)
-#endif
 
 using mg::Lvl;
 typedef __nv_bfloat16 bf16;
@@ -258,11 +255,9 @@ mg_status launch_sweep(mg_handle* h, int lev, const Lvl<T, C>& L, const X* x, co
     // ring (DEEP slots of b, the next iterate and, unless BF16, three coefficients) and the
     // stash (2 values per step of half a column); it must fit the budget
     constexpr int DEEP = SweepPF<T>::deep;
-    constexpr bool STAGE = MG_SWEEP_STAGE != 0;
     const int hsteps = (L.nlev + 1) / 2;
-    const size_t per_thread =
-        (STAGE ? DEEP * (sizeof(B) + sizeof(T) + (sizeof(C) >= 4 ? 3 * sizeof(C) : 0)) : 0) +
-        2 * (size_t)hsteps * sizeof(T);
+    const size_t per_thread = DEEP * (sizeof(B) + sizeof(T) + (sizeof(C) >= 4 ? 3 * sizeof(C) : 0)) +
+                              2 * (size_t)hsteps * sizeof(T);
     const size_t per_block = (size_t)L.nlev * sizeof(T);   // the 1/dz table
     int bd = sweep_block(2 * L.ncol);
     const int cap = (int)((SWEEP_SMEM_MAX - per_block) / per_thread) / 32 * 32;
@@ -270,11 +265,11 @@ mg_status launch_sweep(mg_handle* h, int lev, const Lvl<T, C>& L, const X* x, co
     if (bd > cap) bd = cap;
     const size_t smem = per_thread * bd + per_block;
     if (smem > 48 * 1024)
-        CK(cudaFuncSetAttribute(mg::k_sweep<T, C, MODE, X, B, O, BCOPY, SweepPF<T>::deep, SweepPF<T>::shal, STAGE>,
+        CK(cudaFuncSetAttribute(mg::k_sweep<T, C, MODE, X, B, O, BCOPY, SweepPF<T>::deep, SweepPF<T>::shal>,
                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     const int cols = bd / 2;
     const int grid = (L.ncol + cols - 1) / cols;
-    mg::k_sweep<T, C, MODE, X, B, O, BCOPY, SweepPF<T>::deep, SweepPF<T>::shal, STAGE>
+    mg::k_sweep<T, C, MODE, X, B, O, BCOPY, SweepPF<T>::deep, SweepPF<T>::shal>
         <<<grid, bd, smem, s>>>(L, x, xc, ncol_c, b, bcopy, xo, (T)omega);
     CK(cudaGetLastError());
     return MG_OK;
