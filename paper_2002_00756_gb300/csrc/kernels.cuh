@@ -41,10 +41,6 @@ __device__ __forceinline__ T ldx(const X* p) {
     return (T)__ldg(p);
 }
 
-// correctly rounded reciprocal (the same value as 1 / v, without the general division path)
-__device__ __forceinline__ float recip(float v) { return __frcp_rn(v); }
-__device__ __forceinline__ double recip(double v) { return __drcp_rn(v); }
-
 __device__ __forceinline__ int parent_col(int col, int n) {
     const int nn = n * n, p = col / nn, r = col - p * nn, j = r / n, i = r - j * n, nc = n >> 1;
     return p * nc * nc + (j >> 1) * nc + (i >> 1);
@@ -180,7 +176,7 @@ __global__ void k_sweep(Lvl<T, C> L, const X* __restrict__ x, const T* __restric
     const int nsteps = upper ? nlev - hsteps : hsteps;
     const int dir = upper ? -1 : 1;
     const int kfirst = upper ? nlev - 1 : 0;
-    const int ncol = L.ncol, nf = 2 * ncol;   // element offsets fit in 32 bits (checked at set-up)
+    const size_t ncol = L.ncol, nf = 2 * ncol;
     int nb[4], fo[4], pn[4] = {0, 0, 0, 0}, pc = 0;
 #pragma unroll
     for (int s = 0; s < 4; ++s) {
@@ -206,25 +202,25 @@ __global__ void k_sweep(Lvl<T, C> L, const X* __restrict__ x, const T* __restric
         if (i < nsteps) {
             const int k = kfirst + dir * i;
             const int kn = k + dir;
-            const int o = k * ncol, so = slot * bd + tid;
-            const C* th = L.Th + k * nf;
+            const size_t o = (size_t)k * ncol, so = (size_t)slot * bd + tid;
+            const C* th = L.Th + (size_t)k * nf;
             __pipeline_memcpy_async(rb + so, b + o + c, sizeof(B));
             if (RAW) {
                 const bool in = kn >= 0 && kn < nlev;
-                __pipeline_memcpy_async(rx + so, x + (in ? kn : k) * ncol + c, sizeof(T), in ? 0 : sizeof(T));
+                __pipeline_memcpy_async(rx + so, x + (size_t)(in ? kn : k) * ncol + c, sizeof(T), in ? 0 : sizeof(T));
             }
             if (ASYNC_C) {
                 __pipeline_memcpy_async(rte + so, th + fo[0], sizeof(C));
                 __pipeline_memcpy_async(rtn + so, th + fo[2], sizeof(C));
-                __pipeline_memcpy_async(rtv + so, L.Tv + (upper ? k : k + 1) * ncol + c, sizeof(C));
+                __pipeline_memcpy_async(rtv + so, L.Tv + (size_t)(upper ? k : k + 1) * ncol + c, sizeof(C));
             }
         }
         __pipeline_commit();
     };
     auto load_shal = [&](int i, SweepShal<T>& d) {
         const int k = kfirst + dir * i;
-        const int o = k * ncol, oc = k * ncol_c;
-        const C* th = L.Th + k * nf;
+        const size_t o = (size_t)k * ncol, oc = (size_t)k * ncol_c;
+        const C* th = L.Th + (size_t)k * nf;
         if (RAW) {
             if (!shE) d.xh[0] = ldx<T>(x + o + nb[0]);
             if (!shW) d.xh[1] = ldx<T>(x + o + nb[1]);
@@ -237,14 +233,14 @@ __global__ void k_sweep(Lvl<T, C> L, const X* __restrict__ x, const T* __restric
             d.ch[2] = __ldg(xc + oc + pn[2]);
             d.ch[3] = __ldg(xc + oc + pn[3]);
             const int kn = k + dir;
-            d.cn = (kn >= 0 && kn < nlev) ? __ldg(xc + kn * ncol_c + pc) : T(0);
+            d.cn = (kn >= 0 && kn < nlev) ? __ldg(xc + (size_t)kn * ncol_c + pc) : T(0);
         }
         if (!shWf) d.tw = ldc<T>(th + fo[1]);
         d.ts = ldc<T>(th + fo[3]);
         if (!ASYNC_C) {
             d.te = ldc<T>(th + fo[0]);
             d.tn = ldc<T>(th + fo[2]);
-            d.tv = ldc<T>(L.Tv + (upper ? k : k + 1) * ncol + c);
+            d.tv = ldc<T>(L.Tv + (size_t)(upper ? k : k + 1) * ncol + c);
         }
     };
 
@@ -255,8 +251,8 @@ __global__ void k_sweep(Lvl<T, C> L, const X* __restrict__ x, const T* __restric
     for (int j = 0; j < SHAL; ++j)
         if (j < nsteps) load_shal(j, sr[j]);
     T xprev = T(0), x0 = T(0), tprev = T(0);
-    if (RAW) x0 = ldx<T>(x + kfirst * ncol + c);
-    if (PRO) x0 += __ldg(xc + kfirst * ncol_c + pc);
+    if (RAW) x0 = ldx<T>(x + (size_t)kfirst * ncol + c);
+    if (PRO) x0 += __ldg(xc + (size_t)kfirst * ncol_c + pc);
     T q = T(0), ip = T(0), y = T(0), anext = T(0);
     for (int i0 = 0; i0 < hsteps; i0 += DEEP) {
 #pragma unroll
@@ -264,7 +260,7 @@ __global__ void k_sweep(Lvl<T, C> L, const X* __restrict__ x, const T* __restric
             const int i = i0 + j;
             __pipeline_wait_prior(DEEP - 1);
             __syncwarp();   // every lane's copies of this slot are complete and visible
-            const int so = j * bd + tid;
+            const size_t so = (size_t)j * bd + tid;
             const T bk = (T)rb[so];
             T xn = RAW ? rx[so] : T(0);
             T te = T(0), tn = T(0), tv = T(0), twl = T(0);
@@ -302,7 +298,7 @@ __global__ void k_sweep(Lvl<T, C> L, const X* __restrict__ x, const T* __restric
                 if (shW) xh[1] = xWl;
                 const T tw = shWf ? twl : e.tw;
                 const T rdz = srdz[k];
-                if (BCOPY) bcopy[k * ncol + c] = bk;
+                if (BCOPY) bcopy[(size_t)k * ncol + c] = bk;
                 T r = bk;
                 if (MODE != XM_ZERO) {
                     T hx = te * (x0 - xh[0]);
@@ -316,10 +312,10 @@ __global__ void k_sweep(Lvl<T, C> L, const X* __restrict__ x, const T* __restric
                 q = (T(1) + rA * ((te + tw) + (tn + e.ts))) + m * q;
                 const T p = q + anext;
                 y = r + m * y;
-                ip = recip(p);
+                ip = T(1) / p;
                 const T ei = anext * ip;
-                sc[i * bd + tid] = x0 + omega * (y * ip) - ei * xn;
-                se[i * bd + tid] = ei;
+                sc[(size_t)i * bd + tid] = x0 + omega * (y * ip) - ei * xn;
+                se[(size_t)i * bd + tid] = ei;
                 xprev = x0;
                 x0 = xn;
                 tprev = tv;
@@ -341,11 +337,11 @@ __global__ void k_sweep(Lvl<T, C> L, const X* __restrict__ x, const T* __restric
     if (!active || nsteps == 0) return;
     // xprev holds the iterate at the last level of this half: out = x + omega d there
     T out = xprev + omega * dlt;
-    xo[(kfirst + dir * (nsteps - 1)) * ncol + c] = (O)out;
+    xo[(size_t)(kfirst + dir * (nsteps - 1)) * ncol + c] = (O)out;
 #pragma unroll 4
     for (int i = nsteps - 2; i >= 0; --i) {
-        out = sc[i * bd + tid] + se[i * bd + tid] * out;
-        xo[(kfirst + dir * i) * ncol + c] = (O)out;
+        out = sc[(size_t)i * bd + tid] + se[(size_t)i * bd + tid] * out;
+        xo[(size_t)(kfirst + dir * i) * ncol + c] = (O)out;
     }
 }
 

@@ -601,8 +601,6 @@ mg_status setup_impl(mg_handle* h, const mg_mesh* mesh, const mg_params* prm, co
     if (!mg::build_vgeom(mesh->z_interfaces, nlev, vg).empty()) return MG_ERR_ARG;
     const int ncol0 = hg[0].ncol;
     const size_t N0 = (size_t)nlev * ncol0, NV0 = (size_t)(nlev + 1) * ncol0;
-    // the sweep and restriction kernels index a level with 32-bit element offsets
-    if ((size_t)2 * (nlev + 1) * ncol0 >= ((size_t)1 << 31)) return MG_ERR_UNSUPPORTED;
     std::vector<mg::LevelCoef> co(L);
     co[0].g.assign(g, g + N0);
     for (size_t i = 0; i < N0; ++i)
