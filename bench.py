@@ -39,7 +39,7 @@ UNIT = "ms"
 WORKLOAD = "C192L70 pressure solve: GCR(5) FP64 outer + 4-level FP32 V-cycle, tol 1e-8"
 
 
-SWEEP_VARIANTS = ("plain", "zero", "prolong", "prolong0", "pcr-plain", "pcr-zero", "pcr-prolong", "pcr-prolong0")
+SWEEP_VARIANTS = ("plain", "zero", "prolong", "prolong0")
 
 
 KERNEL_SOURCES = ("kernels.cuh", "krylov.cuh")   # all device code of the library

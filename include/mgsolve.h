@@ -89,16 +89,7 @@ typedef struct {
     int32_t vcycle_precision;    /* MG_FP64 | MG_FP32 | MG_FP32_BF16COEF */
     int32_t gcr_restart;         /* GCR directions kept before a restart, 1..MG_MAX_RESTART */
     int32_t max_iter;            /* Krylov iteration limit */
-    int32_t column_solver;       /* exact tridiagonal solve of the sweep (Eq. jacobi):
-                                    MG_COLUMN_AUTO | MG_COLUMN_THOMAS | MG_COLUMN_PCR */
 } mg_params;
-
-/* column solvers of the block-Jacobi sweep; both solve the column systems exactly */
-enum {
-    MG_COLUMN_AUTO = 0,     /* Thomas on levels with many columns, cyclic reduction on the rest */
-    MG_COLUMN_THOMAS = 1,   /* Thomas algorithm from both column ends, two threads per column */
-    MG_COLUMN_PCR = 2       /* parallel cyclic reduction, one warp per column */
-};
 
 /* mixed-system data (Sec. 3.3-3.4): velocity mass M-bar = I + eps B_w on vertical faces,
  * B_w coupling interior vertical face kf to kf+1 with weight beta_up[kf*ncol+col] and to
@@ -236,8 +227,7 @@ enum {
 typedef struct {
     int32_t kind;      /* MG_K_* */
     int32_t level;     /* multigrid level (0 = finest) */
-    int32_t variant;   /* sweeps: iterate source (0 plain, 1 zero, 2 prolongated, 3 prolongation
-                          only), plus 4 when the columns were solved by cyclic reduction;
+    int32_t variant;   /* sweeps: iterate source, 0 plain, 1 zero, 2 prolongated, 3 prolongation only;
                           fused GCR apply: number of stored directions J; otherwise 0 */
     double bytes;      /* algorithmic bytes of the launch */
     double ms;         /* event-timed duration */

@@ -22,8 +22,6 @@ MG_OK, MG_ERR_ARG, MG_ERR_CUDA, MG_ERR_NOMEM = 0, -1, -2, -3
 MG_ERR_NOT_CONVERGED, MG_ERR_BREAKDOWN, MG_ERR_TIMEOUT, MG_ERR_UNSUPPORTED = -4, -5, -6, -7
 MG_FP64, MG_FP32, MG_FP32_BF16COEF = 0, 1, 2
 PRECISIONS = {"fp64": MG_FP64, "fp32": MG_FP32, "fp32_bf16": MG_FP32_BF16COEF}
-MG_COLUMN_AUTO, MG_COLUMN_THOMAS, MG_COLUMN_PCR = 0, 1, 2
-COLUMN_SOLVERS = {"auto": MG_COLUMN_AUTO, "thomas": MG_COLUMN_THOMAS, "pcr": MG_COLUMN_PCR}
 
 
 class MGError(RuntimeError):
@@ -41,7 +39,7 @@ class _Params(ctypes.Structure):
     _fields_ = [("levels", ctypes.c_int32), ("omega", ctypes.c_double), ("n_pre", ctypes.c_int32),
                 ("n_post", ctypes.c_int32), ("n_coarse", ctypes.c_int32),
                 ("vcycle_precision", ctypes.c_int32), ("gcr_restart", ctypes.c_int32),
-                ("max_iter", ctypes.c_int32), ("column_solver", ctypes.c_int32)]
+                ("max_iter", ctypes.c_int32)]
 
 
 class _Mixed(ctypes.Structure):
@@ -185,7 +183,7 @@ def _check(st: int, what: str):
 def mg_setup(n: int, nlev: int, z_interfaces, g, *, radius: float = 6371.0e3, cs_dt: float = 340.0 * 600.0,
              levels: int = 4, omega: float = 0.8, n_pre: int = 2, n_post: int = 2, n_coarse: int = 4,
              precision: str | int = "fp64", gcr_restart: int = 5, max_iter: int = 200,
-             beta_up=None, beta_dn=None, eps: float = 0.0, column_solver: str | int = "auto") -> Handle:
+             beta_up=None, beta_dn=None, eps: float = 0.0) -> Handle:
     """Build the hierarchy on the current CUDA device (see mg_setup in mgsolve.h)."""
     import torch
     torch.cuda.current_device()   # make sure the device context exists
@@ -195,8 +193,7 @@ def mg_setup(n: int, nlev: int, z_interfaces, g, *, radius: float = 6371.0e3, cs
     gg, gp = _host(g, nlev * ncol, "g")
     mesh = _Mesh(n, nlev, radius, cs_dt, zp)
     prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
-    csol = COLUMN_SOLVERS[column_solver] if isinstance(column_solver, str) else int(column_solver)
-    prm = _Params(levels, omega, n_pre, n_post, n_coarse, prec, gcr_restart, max_iter, csol)
+    prm = _Params(levels, omega, n_pre, n_post, n_coarse, prec, gcr_restart, max_iter)
     mixed = None
     keep = [z, gg]
     if beta_up is not None:

@@ -346,118 +346,6 @@ __global__ void k_sweep(Lvl<T, C> L, const X* __restrict__ x, const T* __restric
 }
 
 // ---------------------------------------------------------------------------------------
-// Block-Jacobi sweep with the column systems solved by parallel cyclic reduction (one warp
-// per column), for small levels where the sequential Thomas walk leaves the GPU idle.
-//   1. lanes take levels k = lane, lane+32, ...: residual r = b - H x, couplings a (to k-1)
-//      and c (to k+1) and the row excess S = 1 + horizontal coefficients, in shared memory;
-//   2. cyclic reduction: each step adds to row i the multiples a_i/b_{i-s} of row i-s and
-//      c_i/b_{i+s} of row i+s, which removes x_{i-s} and x_{i+s}; couplings move to i-2s
-//      and i+2s.  Row sums transform linearly, so the excess is updated as a sum of positive
-//      terms, S_i += (a_i/b_{i-s}) S_{i-s} + (c_i/b_{i+s}) S_{i+s}, and the diagonal
-//      b = S + a + c never cancels (the same property as the pivot-excess Thomas form).
-//      After ceil(log2 nlev) steps every row stands alone: d_i = r_i / S_i;
-//   3. x_out = x + omega d.
-// The result is the exact solve of the same tridiagonal systems (Eq. jacobi), in a
-// different elimination order.
-template <typename T, typename C, int MODE, typename X, typename B, typename O, bool BCOPY>
-__global__ void __launch_bounds__(128) k_sweep_pcr(Lvl<T, C> L, const X* __restrict__ x, const T* __restrict__ xc,
-                                                    int ncol_c, const B* __restrict__ b, T* __restrict__ bcopy,
-                                                    O* __restrict__ xo, T omega, int np) {
-    constexpr bool PRO = (MODE == XM_PROLONG || MODE == XM_PROLONG0);
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-    const int c_raw = blockIdx.x * (blockDim.x >> 5) + wib;
-    const bool active = c_raw < L.ncol;
-    const int c = active ? c_raw : L.ncol - 1;
-    const int nlev = L.nlev;
-    // per warp: two buffers of (S, a, c, r) and the iterate, np >= nlev entries each
-    T* base = reinterpret_cast<T*>(smem_raw) + (size_t)wib * 9 * np;
-    T* Sb[2] = {base, base + 4 * np};
-    T* X0 = base + 8 * np;
-    const size_t ncol = L.ncol, nf = 2 * ncol;
-    int nb[4], fo[4], pn[4] = {0, 0, 0, 0};
-#pragma unroll
-    for (int s = 0; s < 4; ++s) {
-        nb[s] = __ldg(L.nbr + s * ncol + c);
-        fo[s] = __ldg(L.fof + s * ncol + c);
-    }
-    const int pc = PRO ? parent_col(c, L.n) : 0;
-    if (PRO) {
-#pragma unroll
-        for (int s = 0; s < 4; ++s) pn[s] = parent_col(nb[s], L.n);
-    }
-    const T rA = __ldg(L.rA + c);
-    // ---- phase 1 ----
-    for (int k = lane; k < nlev; k += 32) {
-        const size_t o = (size_t)k * ncol, oc = (size_t)k * ncol_c;
-        const C* th = L.Th + (size_t)k * nf;
-        const T te = ldc<T>(th + fo[0]), tw = ldc<T>(th + fo[1]);
-        const T tn = ldc<T>(th + fo[2]), ts = ldc<T>(th + fo[3]);
-        const T tup = ldc<T>(L.Tv + o + ncol + c), tdn = ldc<T>(L.Tv + o + c);
-        const T rdz = __ldg(L.rdz + k);
-        const T bk = (T)__ldg(b + o + c);
-        if (BCOPY && active) bcopy[o + c] = bk;
-        T x0 = T(0), r = bk;
-        if (MODE != XM_ZERO) {
-            x0 = xval<MODE, T>(x, xc, o, oc, c, pc);
-            const T xu = (k + 1 < nlev) ? xval<MODE, T>(x, xc, o + ncol, oc + ncol_c, c, pc) : T(0);
-            const T xd = (k > 0) ? xval<MODE, T>(x, xc, o - ncol, oc - ncol_c, c, pc) : T(0);
-            T hx = te * (x0 - xval<MODE, T>(x, xc, o, oc, nb[0], pn[0]));
-            hx += tw * (x0 - xval<MODE, T>(x, xc, o, oc, nb[1], pn[1]));
-            hx += tn * (x0 - xval<MODE, T>(x, xc, o, oc, nb[2], pn[2]));
-            hx += ts * (x0 - xval<MODE, T>(x, xc, o, oc, nb[3], pn[3]));
-            r -= x0 + (rA * hx + rdz * (tup * (x0 - xu) + tdn * (x0 - xd)));
-        }
-        T* B0 = Sb[0];
-        B0[k] = T(1) + rA * ((te + tw) + (tn + ts));   // S
-        B0[np + k] = rdz * tdn;                         // a: coupling to k-1
-        B0[2 * np + k] = rdz * tup;                     // c: coupling to k+1
-        B0[3 * np + k] = r;
-        X0[k] = x0;
-    }
-    __syncwarp();
-    // ---- phase 2: cyclic reduction ----
-    int cur = 0;
-    for (int st = 1; st < nlev; st <<= 1) {
-        const T* I = Sb[cur];
-        T* Oo = Sb[cur ^ 1];
-        for (int i = lane; i < nlev; i += 32) {
-            T Si = I[i], ai = I[np + i], ci = I[2 * np + i], ri = I[3 * np + i];
-            T an = T(0), cn = T(0);
-            if (i - st >= 0) {
-                const int m = i - st;
-                const T Sm = I[m], am = I[np + m], cm = I[2 * np + m];
-                const T alpha = ai / (Sm + am + cm);
-                Si += alpha * Sm;
-                ri += alpha * I[3 * np + m];
-                an = alpha * am;
-            }
-            if (i + st < nlev) {
-                const int m = i + st;
-                const T Sm = I[m], am = I[np + m], cm = I[2 * np + m];
-                const T gamma = ci / (Sm + am + cm);
-                Si += gamma * Sm;
-                ri += gamma * I[3 * np + m];
-                cn = gamma * cm;
-            }
-            Oo[i] = Si;
-            Oo[np + i] = an;
-            Oo[2 * np + i] = cn;
-            Oo[3 * np + i] = ri;
-        }
-        __syncwarp();
-        cur ^= 1;
-    }
-    // ---- phase 3 ----
-    if (!active) return;
-    const T* F = Sb[cur];
-    for (int k = lane; k < nlev; k += 32) {
-        const T d = F[3 * np + k] / F[k];
-        xo[(size_t)k * ncol + c] = (O)(X0[k] + omega * d);
-    }
-}
-
-// ---------------------------------------------------------------------------------------
 // Residual and restriction (Algorithm 1): bc[k][C] = sum_q w[q][C] (b - H x)[k][child_q],
 // w = area_child / area_C; one thread per coarse column and chunk of kchunk levels (there is
 // no vertical recurrence, so short chunks give many independent threads).

@@ -28,9 +28,6 @@
 #ifndef MG_SWEEP_BLOCK
 #define MG_SWEEP_BLOCK 128
 #endif
-#ifndef MG_PCR_MAX_NCOL
-#define MG_PCR_MAX_NCOL (1 << 17)   // automatic choice: cyclic reduction below this many columns
-#endif
 
 using mg::Lvl;
 typedef __nv_bfloat16 bf16;
@@ -253,20 +250,7 @@ mg_status launch_sweep(mg_handle* h, int lev, const Lvl<T, C>& L, const X* x, co
     if (MODE == mg::XM_PLAIN || MODE == mg::XM_PROLONG) per += sizeof(X);
     if (MODE == mg::XM_PROLONG || MODE == mg::XM_PROLONG0) per += 0.25 * sizeof(T);
     if (BCOPY) per += sizeof(T);
-    const int cs = h ? h->prm.column_solver : MG_COLUMN_THOMAS;
-    const bool pcr = cs == MG_COLUMN_PCR || (cs == MG_COLUMN_AUTO && L.ncol < MG_PCR_MAX_NCOL);
-    Prof pr(h, MG_K_SWEEP, lev, nc * per, s, MODE + (pcr ? 4 : 0));
-    if (pcr) {
-        const int warps = 4;
-        const size_t smem = (size_t)warps * 9 * L.nlev * sizeof(T);
-        if (smem > 48 * 1024)
-            CK(cudaFuncSetAttribute(mg::k_sweep_pcr<T, C, MODE, X, B, O, BCOPY>,
-                                    cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        mg::k_sweep_pcr<T, C, MODE, X, B, O, BCOPY>
-            <<<(L.ncol + warps - 1) / warps, 32 * warps, smem, s>>>(L, x, xc, ncol_c, b, bcopy, xo, (T)omega, L.nlev);
-        CK(cudaGetLastError());
-        return MG_OK;
-    }
+    Prof pr(h, MG_K_SWEEP, lev, nc * per, s, MODE);
     // two threads per column; per thread the shared memory holds the asynchronous-copy
     // ring (DEEP slots of b, the next iterate and, unless BF16, three coefficients) and the
     // stash (2 values per step of half a column); it must fit the budget
@@ -815,7 +799,6 @@ mg_status mg_setup(const mg_mesh* mesh, const mg_params* prm, const double* g, c
     if (!std::isfinite(prm->omega) || prm->n_pre < 0 || prm->n_post < 0 || prm->n_coarse < 1) return MG_ERR_ARG;
     if (prm->vcycle_precision < MG_FP64 || prm->vcycle_precision > MG_FP32_BF16COEF) return MG_ERR_ARG;
     if (prm->gcr_restart < 1 || prm->gcr_restart > MG_MAX_RESTART || prm->max_iter < 1) return MG_ERR_ARG;
-    if (prm->column_solver < MG_COLUMN_AUTO || prm->column_solver > MG_COLUMN_PCR) return MG_ERR_ARG;
     if (mixed && (!mixed->beta_up || !mixed->beta_dn || !std::isfinite(mixed->eps) || mixed->eps < 0.0))
         return MG_ERR_ARG;
     mg_handle* h = new (std::nothrow) mg_handle();
@@ -1044,7 +1027,7 @@ extern "C" mg_status mg_smooth_noalloc(mg_handle* h, int32_t level, const double
     const double* cur = x_in;
     for (int i = 0; i < sweeps; ++i) {
         double* dst = to_out ? x_out : scratch;
-        TRY((sweep_any<double, double, double, double>(h, level, L, cur, (const double*)nullptr, 0, b,
+        TRY((sweep_any<double, double, double, double>(nullptr, level, L, cur, (const double*)nullptr, 0, b,
                                                        nullptr, dst, h->prm.omega, s)));
         cur = dst;
         to_out = !to_out;

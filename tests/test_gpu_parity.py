@@ -94,15 +94,11 @@ def test_level_apply_every_level(mg, name):
         assert np.all(np.abs(host(y) - H.apply(x).ravel()) <= 1e-12 * abs_apply_scale(H, x)), l
 
 
-SOLVERS = ["thomas", "pcr"]
-
-
-@pytest.mark.parametrize("solver", SOLVERS)
 @pytest.mark.parametrize("name", ["c12", "c6l7", "c4l1", "c20l9"])
 @pytest.mark.parametrize("sweeps,start", [(1, "zero"), (2, "zero"), (1, "random"), (3, "random")])
-def test_block_jacobi_sweeps(mg, name, sweeps, start, solver):
+def test_block_jacobi_sweeps(mg, name, sweeps, start):
     cfg, inp, hier = problem(name)
-    h = mg.mg_setup_config(cfg, inp, column_solver=solver)
+    h = mg.mg_setup_config(cfg, inp)
     for l, H in enumerate(hier.levels):
         n = H.mesh.nlev * H.mesh.ncol
         b = syn.normal(7, l, n)
@@ -142,11 +138,10 @@ def test_residual_restrict_and_prolong(mg, name):
         assert np.array_equal(host(xf), (x.reshape(H.shape) + prolongate(fine, xc)).ravel())
 
 
-@pytest.mark.parametrize("solver", SOLVERS)
 @pytest.mark.parametrize("name", list(CASES))
-def test_vcycle_fp64(mg, name, solver):
+def test_vcycle_fp64(mg, name):
     cfg, inp, hier = problem(name)
-    h = mg.mg_setup_config(cfg, inp, column_solver=solver)
+    h = mg.mg_setup_config(cfg, inp)
     b = inp["rhs"]
     x = torch.empty(cfg.ncell, dtype=torch.float64, device="cuda")
     mg.vcycle(h, dev(b), x)
@@ -154,13 +149,11 @@ def test_vcycle_fp64(mg, name, solver):
     assert np.linalg.norm(host(x) - ref) <= 1e-12 * np.linalg.norm(ref)
 
 
-@pytest.mark.parametrize("solver", SOLVERS)
 @pytest.mark.parametrize("n_pre,n_post,n_coarse", [(0, 2, 4), (2, 0, 4), (1, 3, 1), (0, 0, 2), (3, 1, 6)])
-def test_vcycle_smoothing_counts(mg, n_pre, n_post, n_coarse, solver):
+def test_vcycle_smoothing_counts(mg, n_pre, n_post, n_coarse):
     cfg, inp, hier = problem("c20l9")
     h = mg.mg_setup(cfg.n, cfg.nlev, inp["z_if"], inp["g"], radius=cfg.radius, cs_dt=cfg.cs * cfg.dt,
-                    levels=cfg.levels, omega=cfg.omega, n_pre=n_pre, n_post=n_post, n_coarse=n_coarse,
-                    column_solver=solver)
+                    levels=cfg.levels, omega=cfg.omega, n_pre=n_pre, n_post=n_post, n_coarse=n_coarse)
     b = inp["rhs"]
     x = torch.empty(cfg.ncell, dtype=torch.float64, device="cuda")
     mg.vcycle(h, dev(b), x)
@@ -168,18 +161,17 @@ def test_vcycle_smoothing_counts(mg, n_pre, n_post, n_coarse, solver):
     assert np.linalg.norm(host(x) - ref) <= 1e-12 * np.linalg.norm(ref)
 
 
-@pytest.mark.parametrize("solver", SOLVERS)
 @pytest.mark.parametrize("precision,tol", [("fp32", 1e-4), ("fp32_bf16", 5e-2)])
 @pytest.mark.parametrize("name", ["c12", "c20l9", "c5l3"])
-def test_vcycle_reduced_precision(mg, name, precision, tol, solver):
+def test_vcycle_reduced_precision(mg, name, precision, tol):
     cfg, inp, hier = problem(name)
-    h = mg.mg_setup_config(cfg, inp, precision=precision, column_solver=solver)
+    h = mg.mg_setup_config(cfg, inp, precision=precision)
     b = inp["rhs"]
     x = torch.empty(cfg.ncell, dtype=torch.float64, device="cuda")
     mg.vcycle(h, dev(b), x)
     ref = hier.vcycle(b, cfg.omega, cfg.n_pre, cfg.n_post, cfg.n_coarse).ravel()
     err = np.linalg.norm(host(x) - ref) / np.linalg.norm(ref)
-    print(f"{name} {precision} {solver} V-cycle relative error vs FP64 oracle: {err:.3e}")
+    print(f"{name} {precision} V-cycle relative error vs FP64 oracle: {err:.3e}")
     assert err <= tol
 
 
@@ -192,13 +184,12 @@ def _xstar(name):
     return _cache[key]
 
 
-@pytest.mark.parametrize("solver", SOLVERS)
 @pytest.mark.parametrize("precision", ["fp64", "fp32", "fp32_bf16"])
 @pytest.mark.parametrize("name", ["c12", "c20l9", "c5l3"])
-def test_pressure_solve(mg, name, precision, solver):
+def test_pressure_solve(mg, name, precision):
     from oracle.krylov import gcr
     cfg, inp, hier = problem(name)
-    h = mg.mg_setup_config(cfg, inp, precision=precision, column_solver=solver)
+    h = mg.mg_setup_config(cfg, inp, precision=precision)
     x = torch.zeros(cfg.ncell, dtype=torch.float64, device="cuda")
     info = mg.pressure_solve(h, dev(inp["rhs"]), x, tol=1e-10)
     assert info.converged and info.rel_res <= 1e-10
