@@ -118,6 +118,9 @@ typedef struct mg_handle mg_handle;
  *   g      HOST, N background-state factors (cell field layout), g > 0
  *   mixed  NULL for the Helmholtz system alone; otherwise the mixed-system data, which
  *          also scales the vertical Helmholtz coefficients by 1 / lumped mass
+ * Meshes with 2 * (nlev + 1) * 6 n^2 >= 2^32 (more than about 2^31 horizontal-face values
+ * on the finest level, e.g. n > 2240 at nlev = 70) are rejected with MG_ERR_UNSUPPORTED:
+ * the column kernels address a level with 32-bit offsets.
  * On success *out holds a handle to release with mg_destroy.  Synchronous. */
 mg_status mg_setup(const mg_mesh* mesh, const mg_params* params, const double* g,
                    const mg_mixed* mixed, mg_handle** out);

@@ -136,14 +136,26 @@ __global__ void __launch_bounds__(256) k_apply(Lvl<T, C> L, const X* __restrict_
 // group, panel edges) is it loaded.  Those loads, the N and S neighbours, the S face and the
 // prolongation terms run SHAL steps ahead in a register ring; 1/dz comes from a per-block
 // shared table.  Both rings are indexed statically: the step loop is unrolled by DEEP.
+//
+// Addressing: every array the walk touches is reached through a per-thread base pointer
+// (column, neighbour column or face index already added) plus one running 32-bit offset
+// kc = k * ncol (cells; 2 kc for the faces, k * ncol_c for the coarse level), so each
+// access costs one multiply-add of the address; the host guarantees 2 nlev ncol < 2^32.
+// The steps of the walk that need no end-of-column checks (both halves still have DEEP
+// steps to stage) run in a loop without them; the last few run with the checks.
 template <typename T>
 struct SweepShal {
     T xh[4], tw, ts, ch[4], cn;
     T te, tn, tv;   // coefficients narrower than 4 bytes (BF16) travel here instead
 };
 
+// (launched with at most MG_SWEEP_BLOCK threads; four resident blocks is what the shared
+// memory of the large levels allows, so registers are capped to match)
+#ifndef MG_SWEEP_BLOCK
+#define MG_SWEEP_BLOCK 128
+#endif
 template <typename T, typename C, int MODE, typename X, typename B, typename O, bool BCOPY, int DEEP, int SHAL>
-__global__ void k_sweep(Lvl<T, C> L, const X* __restrict__ x, const T* __restrict__ xc,
+__global__ void __launch_bounds__(MG_SWEEP_BLOCK, 4) k_sweep(Lvl<T, C> L, const X* __restrict__ x, const T* __restrict__ xc,
                         int ncol_c, const B* __restrict__ b, T* __restrict__ bcopy,
                         O* __restrict__ xo, T omega) {
     static_assert(DEEP % SHAL == 0, "ring lengths");
@@ -176,7 +188,10 @@ __global__ void k_sweep(Lvl<T, C> L, const X* __restrict__ x, const T* __restric
     const int nsteps = upper ? nlev - hsteps : hsteps;
     const int dir = upper ? -1 : 1;
     const int kfirst = upper ? nlev - 1 : 0;
-    const size_t ncol = L.ncol, nf = 2 * ncol;
+    const unsigned ncol = L.ncol;
+    // offsets of level kfirst and their change per step
+    const unsigned kc0 = (unsigned)kfirst * ncol, kcc0 = (unsigned)kfirst * (unsigned)ncol_c;
+    const unsigned dkc = upper ? 0u - ncol : ncol, dkcc = upper ? 0u - (unsigned)ncol_c : (unsigned)ncol_c;
     int nb[4], fo[4], pn[4] = {0, 0, 0, 0}, pc = 0;
 #pragma unroll
     for (int s = 0; s < 4; ++s) {
@@ -195,132 +210,157 @@ __global__ void k_sweep(Lvl<T, C> L, const X* __restrict__ x, const T* __restric
     const bool shW = g != 0 && nb[1] == c - 1;
     // the W face is the left lane's E face when it is the same face
     const bool shWf = ASYNC_C && shW && fo[1] == __ldg(L.fof + (c > 0 ? c - 1 : 0));
+    // per-thread bases; the face arrays advance by 2 kc, the vertical face towards the next
+    // level of the walk is Tv[k+1] going up and Tv[k] going down
+    const B* pb = b + c;
+    const X* px = x + c;
+    const X* pxh[4] = {x + nb[0], x + nb[1], x + nb[2], x + nb[3]};
+    const C* pth[4] = {L.Th + fo[0], L.Th + fo[1], L.Th + fo[2], L.Th + fo[3]};
+    const C* ptv = L.Tv + c + (upper ? 0u : ncol);
+    const T* pch[4] = {xc + pn[0], xc + pn[1], xc + pn[2], xc + pn[3]};
+    const T* pcc = xc + pc;
 
-    // step i works on level kfirst + dir * i; the vertical face towards the next level in
-    // the walk is Tv[k+1] going up and Tv[k] going down
-    auto stage = [&](int i, int slot) {
-        if (i < nsteps) {
-            const int k = kfirst + dir * i;
-            const int kn = k + dir;
-            const size_t o = (size_t)k * ncol, so = (size_t)slot * bd + tid;
-            const C* th = L.Th + (size_t)k * nf;
-            __pipeline_memcpy_async(rb + so, b + o + c, sizeof(B));
+    auto stage = [&](int i, int slot, unsigned kc, bool chk) {
+        if (!chk || i < nsteps) {
+            const int so = slot * bd + tid;
+            __pipeline_memcpy_async(rb + so, pb + kc, sizeof(B));
             if (RAW) {
-                const bool in = kn >= 0 && kn < nlev;
-                __pipeline_memcpy_async(rx + so, x + (size_t)(in ? kn : k) * ncol + c, sizeof(T), in ? 0 : sizeof(T));
+                const bool in = !chk || i + 1 < nsteps || (upper ? kfirst - i - 1 >= 0 : kfirst + i + 1 < nlev);
+                __pipeline_memcpy_async(rx + so, px + (in ? kc + dkc : kc), sizeof(T), in ? 0 : sizeof(T));
             }
             if (ASYNC_C) {
-                __pipeline_memcpy_async(rte + so, th + fo[0], sizeof(C));
-                __pipeline_memcpy_async(rtn + so, th + fo[2], sizeof(C));
-                __pipeline_memcpy_async(rtv + so, L.Tv + (size_t)(upper ? k : k + 1) * ncol + c, sizeof(C));
+                __pipeline_memcpy_async(rte + so, pth[0] + 2 * kc, sizeof(C));
+                __pipeline_memcpy_async(rtn + so, pth[2] + 2 * kc, sizeof(C));
+                __pipeline_memcpy_async(rtv + so, ptv + kc, sizeof(C));
             }
         }
         __pipeline_commit();
     };
-    auto load_shal = [&](int i, SweepShal<T>& d) {
-        const int k = kfirst + dir * i;
-        const size_t o = (size_t)k * ncol, oc = (size_t)k * ncol_c;
-        const C* th = L.Th + (size_t)k * nf;
+    auto load_shal = [&](int i, unsigned kc, unsigned kcc, SweepShal<T>& d) {
         if (RAW) {
-            if (!shE) d.xh[0] = ldx<T>(x + o + nb[0]);
-            if (!shW) d.xh[1] = ldx<T>(x + o + nb[1]);
-            d.xh[2] = ldx<T>(x + o + nb[2]);
-            d.xh[3] = ldx<T>(x + o + nb[3]);
+            if (!shE) d.xh[0] = ldx<T>(pxh[0] + kc);
+            if (!shW) d.xh[1] = ldx<T>(pxh[1] + kc);
+            d.xh[2] = ldx<T>(pxh[2] + kc);
+            d.xh[3] = ldx<T>(pxh[3] + kc);
         }
         if (PRO) {
-            if (!shE) d.ch[0] = __ldg(xc + oc + pn[0]);
-            if (!shW) d.ch[1] = __ldg(xc + oc + pn[1]);
-            d.ch[2] = __ldg(xc + oc + pn[2]);
-            d.ch[3] = __ldg(xc + oc + pn[3]);
-            const int kn = k + dir;
-            d.cn = (kn >= 0 && kn < nlev) ? __ldg(xc + (size_t)kn * ncol_c + pc) : T(0);
+            if (!shE) d.ch[0] = __ldg(pch[0] + kcc);
+            if (!shW) d.ch[1] = __ldg(pch[1] + kcc);
+            d.ch[2] = __ldg(pch[2] + kcc);
+            d.ch[3] = __ldg(pch[3] + kcc);
+            const int k = kfirst + dir * i, kn = k + dir;
+            d.cn = (kn >= 0 && kn < nlev) ? __ldg(pcc + (kcc + dkcc)) : T(0);   // offsets wrap mod 2^32: add them first
         }
-        if (!shWf) d.tw = ldc<T>(th + fo[1]);
-        d.ts = ldc<T>(th + fo[3]);
+        if (!shWf) d.tw = ldc<T>(pth[1] + 2 * kc);
+        d.ts = ldc<T>(pth[3] + 2 * kc);
         if (!ASYNC_C) {
-            d.te = ldc<T>(th + fo[0]);
-            d.tn = ldc<T>(th + fo[2]);
-            d.tv = ldc<T>(L.Tv + (size_t)(upper ? k : k + 1) * ncol + c);
+            d.te = ldc<T>(pth[0] + 2 * kc);
+            d.tn = ldc<T>(pth[2] + 2 * kc);
+            d.tv = ldc<T>(ptv + kc);
         }
     };
 
+    unsigned kc_st = kc0;   // offset of the next level to stage
 #pragma unroll
-    for (int j = 0; j < DEEP; ++j) stage(j, j);
+    for (int j = 0; j < DEEP; ++j) {
+        stage(j, j, kc_st, true);
+        kc_st += dkc;
+    }
     SweepShal<T> sr[SHAL];
+    unsigned kc_sh = kc0, kcc_sh = kcc0;   // offsets of the next level for the register ring
 #pragma unroll
-    for (int j = 0; j < SHAL; ++j)
-        if (j < nsteps) load_shal(j, sr[j]);
+    for (int j = 0; j < SHAL; ++j) {
+        if (j < nsteps) load_shal(j, kc_sh, kcc_sh, sr[j]);
+        kc_sh += dkc;
+        kcc_sh += dkcc;
+    }
     T xprev = T(0), x0 = T(0), tprev = T(0);
-    if (RAW) x0 = ldx<T>(x + (size_t)kfirst * ncol + c);
-    if (PRO) x0 += __ldg(xc + (size_t)kfirst * ncol_c + pc);
+    if (RAW) x0 = ldx<T>(px + kc0);
+    if (PRO) x0 += __ldg(pcc + kcc0);
     T q = T(0), ip = T(0), y = T(0), anext = T(0);
-    for (int i0 = 0; i0 < hsteps; i0 += DEEP) {
-#pragma unroll
-        for (int j = 0; j < DEEP; ++j) {
-            const int i = i0 + j;
-            __pipeline_wait_prior(DEEP - 1);
-            __syncwarp();   // every lane's copies of this slot are complete and visible
-            const size_t so = (size_t)j * bd + tid;
-            const T bk = (T)rb[so];
-            T xn = RAW ? rx[so] : T(0);
-            T te = T(0), tn = T(0), tv = T(0), twl = T(0);
-            if (ASYNC_C) {
-                te = (T)rte[so];
-                tn = (T)rtn[so];
-                tv = (T)rtv[so];
-                if (shWf) twl = (T)rte[so - 1];
-            }
-            __syncwarp();   // reads of the slot are done before it is refilled
-            stage(i + DEEP, j);
-            // neighbour iterates at this level from the adjacent lanes (all lanes take part)
-            const T xEl = __shfl_down_sync(0xffffffffu, x0, 1);
-            const T xWl = __shfl_up_sync(0xffffffffu, x0, 1);
-            if (i < nsteps) {
-                const SweepShal<T> e = sr[j % SHAL];
-                if (!ASYNC_C) {
-                    te = e.te;
-                    tn = e.tn;
-                    tv = e.tv;
-                }
-                if (i + SHAL < nsteps) load_shal(i + SHAL, sr[j % SHAL]);
-                const int k = kfirst + dir * i;
-                if (PRO) xn += e.cn;
-                T xh[4] = {T(0), T(0), T(0), T(0)};
-                if (RAW) {
-#pragma unroll
-                    for (int s = 0; s < 4; ++s) xh[s] = e.xh[s];
-                }
-                if (PRO) {
-#pragma unroll
-                    for (int s = 0; s < 4; ++s) xh[s] += e.ch[s];
-                }
-                if (shE) xh[0] = xEl;
-                if (shW) xh[1] = xWl;
-                const T tw = shWf ? twl : e.tw;
-                const T rdz = srdz[k];
-                if (BCOPY) bcopy[(size_t)k * ncol + c] = bk;
-                T r = bk;
-                if (MODE != XM_ZERO) {
-                    T hx = te * (x0 - xh[0]);
-                    hx += tw * (x0 - xh[1]);
-                    hx += tn * (x0 - xh[2]);
-                    hx += e.ts * (x0 - xh[3]);
-                    r -= x0 + (rA * hx + rdz * (tv * (x0 - xn) + tprev * (x0 - xprev)));
-                }
-                anext = rdz * tv;
-                const T m = (rdz * tprev) * ip;
-                q = (T(1) + rA * ((te + tw) + (tn + e.ts))) + m * q;
-                const T p = q + anext;
-                y = r + m * y;
-                ip = T(1) / p;
-                const T ei = anext * ip;
-                sc[(size_t)i * bd + tid] = x0 + omega * (y * ip) - ei * xn;
-                se[(size_t)i * bd + tid] = ei;
-                xprev = x0;
-                x0 = xn;
-                tprev = tv;
-            }
+    T* psc = sc + tid;
+    T* pse = se + tid;
+    const T* prdz = srdz + kfirst;
+
+    auto step = [&](int i, int j, bool chk) {
+        __pipeline_wait_prior(DEEP - 1);
+        __syncwarp();   // every lane's copies of this slot are complete and visible
+        const int so = j * bd + tid;
+        const T bk = (T)rb[so];
+        T xn = RAW ? rx[so] : T(0);
+        T te = T(0), tn = T(0), tv = T(0), twl = T(0);
+        if (ASYNC_C) {
+            te = (T)rte[so];
+            tn = (T)rtn[so];
+            tv = (T)rtv[so];
+            if (shWf) twl = (T)rte[so - 1];
         }
+        __syncwarp();   // reads of the slot are done before it is refilled
+        stage(i + DEEP, j, kc_st, chk);
+        kc_st += dkc;
+        // neighbour iterates at this level from the adjacent lanes (all lanes take part)
+        const T xEl = __shfl_down_sync(0xffffffffu, x0, 1);
+        const T xWl = __shfl_up_sync(0xffffffffu, x0, 1);
+        if (!chk || i < nsteps) {
+            const SweepShal<T> e = sr[j % SHAL];
+            if (!ASYNC_C) {
+                te = e.te;
+                tn = e.tn;
+                tv = e.tv;
+            }
+            if (!chk || i + SHAL < nsteps) load_shal(i + SHAL, kc_sh, kcc_sh, sr[j % SHAL]);
+            if (PRO) xn += e.cn;
+            T xh[4] = {T(0), T(0), T(0), T(0)};
+            if (RAW) {
+#pragma unroll
+                for (int s = 0; s < 4; ++s) xh[s] = e.xh[s];
+            }
+            if (PRO) {
+#pragma unroll
+                for (int s = 0; s < 4; ++s) xh[s] += e.ch[s];
+            }
+            if (shE) xh[0] = xEl;
+            if (shW) xh[1] = xWl;
+            const T tw = shWf ? twl : e.tw;
+            const T rdz = *prdz;
+            if (BCOPY) bcopy[kc_sh - SHAL * dkc + c] = bk;
+            T r = bk;
+            if (MODE != XM_ZERO) {
+                T hx = te * (x0 - xh[0]);
+                hx += tw * (x0 - xh[1]);
+                hx += tn * (x0 - xh[2]);
+                hx += e.ts * (x0 - xh[3]);
+                r -= x0 + (rA * hx + rdz * (tv * (x0 - xn) + tprev * (x0 - xprev)));
+            }
+            anext = rdz * tv;
+            const T m = (rdz * tprev) * ip;
+            q = (T(1) + rA * ((te + tw) + (tn + e.ts))) + m * q;
+            const T p = q + anext;
+            y = r + m * y;
+            ip = T(1) / p;
+            const T ei = anext * ip;
+            *psc = x0 + omega * (y * ip) - ei * xn;
+            *pse = ei;
+            xprev = x0;
+            x0 = xn;
+            tprev = tv;
+        }
+        psc += bd;
+        pse += bd;
+        prdz += dir;
+        kc_sh += dkc;
+        kcc_sh += dkcc;
+    };
+    // steady state: every step of both halves stages DEEP ahead and loads SHAL ahead
+    const int nfree = nlev - hsteps - DEEP;   // steps i < nfree need no checks in either half
+    int i0 = 0;
+    for (; i0 + DEEP <= nfree; i0 += DEEP) {
+#pragma unroll
+        for (int j = 0; j < DEEP; ++j) step(i0 + j, j, false);
+    }
+    for (; i0 < hsteps; i0 += DEEP) {
+#pragma unroll
+        for (int j = 0; j < DEEP; ++j) step(i0 + j, j, true);
     }
     __pipeline_wait_prior(0);
     // interface rows h-1 (lower half) and h (upper half)
@@ -337,11 +377,19 @@ __global__ void k_sweep(Lvl<T, C> L, const X* __restrict__ x, const T* __restric
     if (!active || nsteps == 0) return;
     // xprev holds the iterate at the last level of this half: out = x + omega d there
     T out = xprev + omega * dlt;
-    xo[(size_t)(kfirst + dir * (nsteps - 1)) * ncol + c] = (O)out;
+    O* po = xo + c;
+    unsigned ko = kc0 + (unsigned)(nsteps - 1) * dkc;
+    po[ko] = (O)out;
+    if (nsteps < 2) return;
+    const T* qsc = sc + (nsteps - 2) * bd + tid;
+    const T* qse = se + (nsteps - 2) * bd + tid;
 #pragma unroll 4
     for (int i = nsteps - 2; i >= 0; --i) {
-        out = sc[(size_t)i * bd + tid] + se[(size_t)i * bd + tid] * out;
-        xo[(size_t)(kfirst + dir * i) * ncol + c] = (O)out;
+        out = *qsc + *qse * out;
+        ko -= dkc;
+        po[ko] = (O)out;
+        qsc -= bd;
+        qse -= bd;
     }
 }
 

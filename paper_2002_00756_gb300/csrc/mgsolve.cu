@@ -25,6 +25,9 @@
 #ifndef MG_SWEEP_SHAL32
 #define MG_SWEEP_SHAL32 4
 #endif
+#ifndef MG_SWEEP_SHAL_PRO
+#define MG_SWEEP_SHAL_PRO 2
+#endif
 #ifndef MG_SWEEP_BLOCK
 #define MG_SWEEP_BLOCK 128
 #endif
@@ -264,13 +267,14 @@ mg_status launch_sweep(mg_handle* h, int lev, const Lvl<T, C>& L, const X* x, co
     if (cap < 32) return MG_ERR_UNSUPPORTED;
     if (bd > cap) bd = cap;
     const size_t smem = per_thread * bd + per_block;
-    if (smem > 48 * 1024)
-        CK(cudaFuncSetAttribute(mg::k_sweep<T, C, MODE, X, B, O, BCOPY, SweepPF<T>::deep, SweepPF<T>::shal>,
-                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    // a prolongation sweep with a fine iterate carries eight neighbour values per step:
+    // its register ring is shorter so that it fits the register budget
+    constexpr int SHAL = MODE == mg::XM_PROLONG ? MG_SWEEP_SHAL_PRO : SweepPF<T>::shal;
+    auto kern = mg::k_sweep<T, C, MODE, X, B, O, BCOPY, DEEP, SHAL>;
+    if (smem > 48 * 1024) CK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     const int cols = bd / 2;
     const int grid = (L.ncol + cols - 1) / cols;
-    mg::k_sweep<T, C, MODE, X, B, O, BCOPY, SweepPF<T>::deep, SweepPF<T>::shal>
-        <<<grid, bd, smem, s>>>(L, x, xc, ncol_c, b, bcopy, xo, (T)omega);
+    kern<<<grid, bd, smem, s>>>(L, x, xc, ncol_c, b, bcopy, xo, (T)omega);
     CK(cudaGetLastError());
     return MG_OK;
 }
@@ -801,6 +805,8 @@ mg_status mg_setup(const mg_mesh* mesh, const mg_params* prm, const double* g, c
     if (prm->gcr_restart < 1 || prm->gcr_restart > MG_MAX_RESTART || prm->max_iter < 1) return MG_ERR_ARG;
     if (mixed && (!mixed->beta_up || !mixed->beta_dn || !std::isfinite(mixed->eps) || mixed->eps < 0.0))
         return MG_ERR_ARG;
+    // the column kernels address a level with 32-bit offsets (horizontal faces: 2 kc)
+    if (2.0 * (mesh->nlev + 1) * 6.0 * (double)mesh->n * mesh->n >= 4294967296.0) return MG_ERR_UNSUPPORTED;
     mg_handle* h = new (std::nothrow) mg_handle();
     if (!h) return MG_ERR_NOMEM;
     mg_status st = setup_impl(h, mesh, prm, g, mixed);

@@ -175,6 +175,30 @@ def test_vcycle_reduced_precision(mg, name, precision, tol):
     assert err <= tol
 
 
+# 6 * 66^2 = 26136 columns: FP32 sweeps with the full 128-thread blocks of the large
+# levels and a ragged last block (26136 = 408 * 64 + 24 columns), an odd column height
+# (9: the upper half of each column is one level shorter) and an odd coarse n (33).  FP32
+# rounding reaches the V-cycle result at about 1e-7 relative; a wrong neighbour or
+# coefficient in any part of the mesh is far above the 2e-6 allowed here.
+CASES["c66l9"] = (syn.small_config(66, 9, levels=2, seed=syn.BASE_SEED + 15), None)
+
+
+@pytest.mark.parametrize("n_pre,n_post,n_coarse", [(2, 2, 4), (0, 2, 4), (1, 3, 1), (2, 0, 2)])
+def test_vcycle_fp32_large_ragged_level(mg, n_pre, n_post, n_coarse):
+    cfg, inp, hier = problem("c66l9")
+    assert cfg.ncol >= 128 * 150 and cfg.ncol % 64 != 0 and cfg.nlev % 2 == 1
+    h = mg.mg_setup(cfg.n, cfg.nlev, inp["z_if"], inp["g"], radius=cfg.radius, cs_dt=cfg.cs * cfg.dt,
+                    levels=cfg.levels, omega=cfg.omega, n_pre=n_pre, n_post=n_post, n_coarse=n_coarse,
+                    precision="fp32")
+    b = inp["rhs"]
+    x = torch.empty(cfg.ncell, dtype=torch.float64, device="cuda")
+    mg.vcycle(h, dev(b), x)
+    ref = hier.vcycle(b, cfg.omega, n_pre, n_post, n_coarse).ravel()
+    err = np.linalg.norm(host(x) - ref) / np.linalg.norm(ref)
+    print(f"c66l9 fp32 V-cycle ({n_pre},{n_post},{n_coarse}) relative error vs FP64 oracle: {err:.3e}")
+    assert err <= 2e-6
+
+
 def _xstar(name):
     from oracle.reference import assemble_helmholtz, direct_solve
     cfg, inp, hier = problem(name)
