@@ -42,7 +42,7 @@ WORKLOAD = "C192L70 pressure solve: GCR(5) FP64 outer + 4-level FP32 V-cycle, to
 SWEEP_VARIANTS = ("plain", "zero", "prolong", "prolong0")
 
 
-KERNEL_SOURCES = ("kernels.cuh", "krylov.cuh")   # all device code of the library
+KERNEL_SOURCES = ("kernels.cuh", "krylov.cuh", "mgsolve.cu")   # device code and launch configurations
 
 
 def _source_digest() -> str:

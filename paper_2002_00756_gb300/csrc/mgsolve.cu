@@ -28,6 +28,9 @@
 #ifndef MG_SWEEP_SHAL_PRO
 #define MG_SWEEP_SHAL_PRO 2
 #endif
+#ifndef MG_SWEEP_SHAL_ZERO
+#define MG_SWEEP_SHAL_ZERO 2
+#endif
 #ifndef MG_SWEEP_BLOCK
 #define MG_SWEEP_BLOCK 128
 #endif
@@ -267,9 +270,12 @@ mg_status launch_sweep(mg_handle* h, int lev, const Lvl<T, C>& L, const X* x, co
     if (cap < 32) return MG_ERR_UNSUPPORTED;
     if (bd > cap) bd = cap;
     const size_t smem = per_thread * bd + per_block;
-    // a prolongation sweep with a fine iterate carries eight neighbour values per step:
-    // its register ring is shorter so that it fits the register budget
-    constexpr int SHAL = MODE == mg::XM_PROLONG ? MG_SWEEP_SHAL_PRO : SweepPF<T>::shal;
+    // ring lengths per iterate source (measured at C192L70): a prolongation sweep with a fine
+    // iterate carries eight neighbour values per step and needs the shorter ring to fit the
+    // register budget; the zero-start sweep is fastest with the shorter ring as well
+    constexpr int SHAL = MODE == mg::XM_PROLONG ? MG_SWEEP_SHAL_PRO
+                         : MODE == mg::XM_ZERO    ? (sizeof(T) == 8 ? 2 : MG_SWEEP_SHAL_ZERO)
+                                                  : SweepPF<T>::shal;
     auto kern = mg::k_sweep<T, C, MODE, X, B, O, BCOPY, DEEP, SHAL>;
     if (smem > 48 * 1024) CK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     const int cols = bd / 2;
