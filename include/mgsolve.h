@@ -236,8 +236,11 @@ typedef struct {
     double ms;         /* event-timed duration */
 } mg_kernel_record;
 
-/* Start recording up to `capacity` launches (creates the events; not a solve call). */
-mg_status mg_profile_start(mg_handle* h, int32_t capacity);
+/* Start recording up to `capacity` launches (creates the events; not a solve call).  Only
+ * launches of the given kind (MG_K_*) and multigrid level are recorded; -1 for either
+ * records all kinds or all levels.  Every recorded launch adds two event records to its
+ * stream, so a narrow selection keeps the recording cheap inside a timed region. */
+mg_status mg_profile_start(mg_handle* h, int32_t capacity, int32_t kind, int32_t level);
 
 /* Stop recording, synchronise the device and copy up to `cap` records to `out` (HOST);
  * *count receives the number recorded (launches beyond the capacity are not timed). */

@@ -79,7 +79,7 @@ _SIGS = {
     "mg_prolong_add": [_VP, _I32, _DP, _DP, _VP],
     "mixed_apply": [_VP, _DP, _DP, _DP, _DP, _VP],
     "schur_precond": [_VP, _DP, _DP, _DP, _DP, _VP],
-    "mg_profile_start": [_VP, _I32],
+    "mg_profile_start": [_VP, _I32, _I32, _I32],
     "mg_profile_stop": [_VP, ctypes.POINTER(_KRec), _I32, ctypes.POINTER(ctypes.c_int32)],
 }
 
@@ -306,9 +306,11 @@ def schur_precond(h: Handle, ru, rp, u, p, stream=None):
                                 _ptr(p, h.ncell, "p"), _stream(stream)), "schur_precond")
 
 
-def mg_profile_start(h: Handle, capacity: int = 65536):
-    """Record every kernel launch of the following calls with CUDA events."""
-    _check(load().mg_profile_start(h.ptr, capacity), "mg_profile_start")
+def mg_profile_start(h: Handle, capacity: int = 65536, kind: str | None = None, level: int | None = None):
+    """Record the kernel launches of the following calls with CUDA events (all of them, or
+    only those of one kind, e.g. "sweep", and / or one multigrid level)."""
+    k = -1 if kind is None else KERNEL_KINDS.index(kind)
+    _check(load().mg_profile_start(h.ptr, capacity, k, -1 if level is None else level), "mg_profile_start")
     h._prof_cap = capacity
 
 

@@ -11,6 +11,11 @@
 
 #include "kernels.cuh"
 
+// fused GCR apply in diagonal form (1) or difference form (0)
+#ifndef MG_APPLY_DIAG
+#define MG_APPLY_DIAG 1
+#endif
+
 namespace mg {
 
 constexpr int RED_THREADS = 256;
@@ -303,6 +308,16 @@ __global__ void __launch_bounds__(RED_THREADS) k_apply_gcr(Lvl<double, double> L
         for (int k = k0; k < k1; ++k) {
             const size_t o = (size_t)k * ncol, e = o + c;
             const double xp = (k + 1 < L.nlev) ? __ldg(z + o + ncol + c) : 0.0;
+#if MG_APPLY_DIAG
+            // diagonal form: (1 + sum_f a_f) x_i - sum_f a_f x_j, 7 FP64 operations
+            double we = __ldg(a6 + 6 * N + e) * x0;
+            we = fma(-__ldg(a6 + e), __ldg(z + o + nb[0]), we);
+            we = fma(-__ldg(a6 + N + e), __ldg(z + o + nb[1]), we);
+            we = fma(-__ldg(a6 + 2 * N + e), __ldg(z + o + nb[2]), we);
+            we = fma(-__ldg(a6 + 3 * N + e), __ldg(z + o + nb[3]), we);
+            we = fma(-__ldg(a6 + 4 * N + e), xp, we);
+            we = fma(-__ldg(a6 + 5 * N + e), xm, we);
+#else
             double we = x0;
             we = fma(__ldg(a6 + e), x0 - __ldg(z + o + nb[0]), we);
             we = fma(__ldg(a6 + N + e), x0 - __ldg(z + o + nb[1]), we);
@@ -310,6 +325,7 @@ __global__ void __launch_bounds__(RED_THREADS) k_apply_gcr(Lvl<double, double> L
             we = fma(__ldg(a6 + 3 * N + e), x0 - __ldg(z + o + nb[3]), we);
             we = fma(__ldg(a6 + 4 * N + e), x0 - xp, we);
             we = fma(__ldg(a6 + 5 * N + e), x0 - xm, we);
+#endif
             w[e] = we;
             gcr_accumulate<J>(v, we, __ldg(r + e), Wb, ld, e);
             xm = x0;

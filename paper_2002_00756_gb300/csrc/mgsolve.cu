@@ -25,6 +25,13 @@
 #ifndef MG_SWEEP_SHAL32
 #define MG_SWEEP_SHAL32 4
 #endif
+// residual + restriction on levels with n % 16 == 0: levels per thread, levels loaded ahead
+#ifndef MG_RESTRICT_KCHUNK
+#define MG_RESTRICT_KCHUNK 8
+#endif
+#ifndef MG_RESTRICT_SHAL
+#define MG_RESTRICT_SHAL 2
+#endif
 #ifndef MG_SWEEP_SHAL_PRO
 #define MG_SWEEP_SHAL_PRO 2
 #endif
@@ -73,7 +80,7 @@ struct mg_handle {
     std::vector<DevLevel> lv;
     double* rdz64 = nullptr;
     float* rdz32 = nullptr;
-    double* a6 = nullptr;       // finest level: six premultiplied FP64 couplings per cell
+    double* a6 = nullptr;       // finest level: six premultiplied FP64 couplings and 1 + their sum, per cell
     // GCR
     size_t glen = 0;            // length of a GCR vector (N, or nu + N with mixed data)
     double* Z = nullptr;        // [restart][glen]
@@ -100,6 +107,7 @@ struct mg_handle {
         double bytes;
     };
     bool prof = false;
+    int prof_kind = -1, prof_level = -1;   // record only this kind / level (-1: all)
     std::vector<cudaEvent_t> evpool;
     std::vector<Rec> recs;
 };
@@ -171,7 +179,8 @@ struct Prof {
     cudaStream_t s;
     int idx = -1;
     Prof(mg_handle* h_, int kind, int level, double bytes, cudaStream_t s_, int variant = 0) : h(h_), s(s_) {
-        if (h && h->prof && 2 * (h->recs.size() + 1) <= h->evpool.size()) {
+        if (h && h->prof && 2 * (h->recs.size() + 1) <= h->evpool.size() &&
+            (h->prof_kind < 0 || h->prof_kind == kind) && (h->prof_level < 0 || h->prof_level == level)) {
             idx = (int)h->recs.size();
             h->recs.push_back({kind, level, variant, bytes});
             cudaEventRecord(h->evpool[2 * idx], s);
@@ -294,9 +303,10 @@ mg_status launch_restrict(mg_handle* h, int lev, const Lvl<T, C>& L, const X* x,
     if (L.n % 16 == 0) {
         // one thread per fine column, 4 warps per block
         const int warps = 6 * (L.n / 2) * (L.n / 16);
-        const int kc = APPLY_KCHUNK;
+        const int kc = MG_RESTRICT_KCHUNK;
         const dim3 grid((warps + 3) / 4, (L.nlev + kc - 1) / kc);
-        mg::k_resid_restrict16<T, C, XZERO, X, B, O, 2><<<grid, 128, 0, s>>>(L, x, b, w, bc, ncol_c, kc);
+        mg::k_resid_restrict16<T, C, XZERO, X, B, O, MG_RESTRICT_SHAL><<<grid, 128, 0, s>>>(L, x, b, w, bc, ncol_c,
+                                                                                           kc);
         CK(cudaGetLastError());
         return MG_OK;
     }
@@ -448,7 +458,8 @@ struct RunApplyGcr {
     static mg_status run(mg_handle* h, const double* z, double* w, cudaStream_t s) {
         const Lvl<double, double> L = View<double, double>::lvl(h, 0);
         const double nc = (double)L.nlev * L.ncol;
-        Prof pr(h, MG_K_APPLY, 0, nc * 8.0 * (1 + 6 + 1 + 1 + J), s, J);   // z, 6 couplings, w, r, w_i
+        // z, the couplings (6, and the diagonal in diagonal form), w, r, w_i
+        Prof pr(h, MG_K_APPLY, 0, nc * 8.0 * (1 + 6 + MG_APPLY_DIAG + 1 + 1 + J), s, J);
         const int kc = GCR_APPLY_KCHUNK;
         dim3 grid((L.ncol + mg::RED_THREADS - 1) / mg::RED_THREADS, (L.nlev + kc - 1) / kc);
         mg::k_apply_gcr<J><<<grid, mg::RED_THREADS, 0, s>>>(L, h->a6, z, w, h->W, h->glen, h->r, kc, h->partials,
@@ -686,10 +697,11 @@ mg_status setup_impl(mg_handle* h, const mg_mesh* mesh, const mg_params* prm, co
         }
     }
     {
-        // finest level: a_side = Th[k][face] / area, a_up = Tv[k+1] / dz, a_dn = Tv[k] / dz
+        // finest level: a_side = Th[k][face] / area, a_up = Tv[k+1] / dz, a_dn = Tv[k] / dz,
+        // and the diagonal 1 + sum of the six
         const mg::HGeom& G = hg[0];
         const size_t N = (size_t)nlev * ncol0;
-        std::vector<double> a6(6 * N);
+        std::vector<double> a6(7 * N);
         for (int k = 0; k < nlev; ++k)
             for (int c = 0; c < ncol0; ++c) {
                 const size_t e = (size_t)k * ncol0 + c;
@@ -698,6 +710,9 @@ mg_status setup_impl(mg_handle* h, const mg_mesh* mesh, const mg_params* prm, co
                     a6[sd * N + e] = co[0].Th[(size_t)k * 2 * ncol0 + G.face_of[sd * ncol0 + c]] * rA;
                 a6[4 * N + e] = co[0].Tv[(size_t)(k + 1) * ncol0 + c] * rdz[k];
                 a6[5 * N + e] = co[0].Tv[(size_t)k * ncol0 + c] * rdz[k];
+                double d = 1.0;
+                for (int f = 0; f < 6; ++f) d += a6[f * N + e];
+                a6[6 * N + e] = d;
             }
         TRY(upload(h, &h->a6, a6));
     }
@@ -944,8 +959,10 @@ mg_status schur_precond(mg_handle* h, const double* ru, const double* rp, double
     return schur_impl(h, ru, rp, u, p, S(stream));
 }
 
-mg_status mg_profile_start(mg_handle* h, int32_t capacity) {
+mg_status mg_profile_start(mg_handle* h, int32_t capacity, int32_t kind, int32_t level) {
     if (!h || capacity < 1 || capacity > (1 << 20)) return MG_ERR_ARG;
+    h->prof_kind = kind < 0 ? -1 : kind;
+    h->prof_level = level < 0 ? -1 : level;
     DeviceGuard dg(h->device);
     while ((int)h->evpool.size() < 2 * capacity) {
         cudaEvent_t e;
