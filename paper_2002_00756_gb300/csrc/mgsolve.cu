@@ -92,6 +92,12 @@ struct mg_handle {
     unsigned int* tickets = nullptr;
     double* host_sc = nullptr;  // pinned
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    // one CUDA graph per GCR slot j and system (0 pressure, 1 mixed): the V-cycle, the
+    // operator with its sums, the orthogonalisation and the read-back of <r, r>, captured on
+    // `cap` the first time and replayed on the caller's stream afterwards
+    cudaStream_t cap = nullptr;
+    cudaGraphExec_t gexec[2][mg::MAXR] = {};
+    bool graphs_off = false;
     int red_grid = 0;
     // mixed
     bool mixed = false;
@@ -498,8 +504,26 @@ mg_status apply_gcr(mg_handle* h, const double* z, double* w, int j, cudaStream_
     return dispatch_j<RunApplyGcr>(j, h, z, w, s);
 }
 
+// Capture the launches of `body` into *out (left null, and graphs switched off for the
+// handle, if the capture or the instantiation fails; the caller then launches directly).
+template <typename Body>
+void capture_graph(mg_handle* h, Body& body, cudaGraphExec_t* out) {
+    *out = nullptr;
+    cudaGraph_t g = nullptr;
+    if (cudaStreamBeginCapture(h->cap, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+        const mg_status st = body(h->cap);
+        const cudaError_t e = cudaStreamEndCapture(h->cap, &g);
+        if (st == MG_OK && e == cudaSuccess && g && cudaGraphInstantiate(out, g, 0) != cudaSuccess) *out = nullptr;
+        if (g) cudaGraphDestroy(g);
+    }
+    if (!*out) {
+        h->graphs_off = true;
+        cudaGetLastError();
+    }
+}
+
 template <typename ApplyAS, typename ApplyP>
-mg_status gcr(mg_handle* h, size_t n, const double* b, double* x, double tol, mg_solve_info* info,
+mg_status gcr(mg_handle* h, int sys, size_t n, const double* b, double* x, double tol, mg_solve_info* info,
               cudaStream_t s, ApplyAS applyAS, ApplyP applyP) {
     const int m = h->prm.gcr_restart;
     const int G = h->red_grid;
@@ -525,10 +549,19 @@ mg_status gcr(mg_handle* h, size_t n, const double* b, double* x, double tol, mg
             const int j = it % m;
             double* z = h->Z + (size_t)j * h->glen;
             double* w = h->W + (size_t)j * h->glen;
-            TRY(applyP(h->r, z));
-            TRY(applyAS(z, w, j));
-            TRY(dispatch_j<RunOrth>(j, h, n, s));
-            CK(cudaMemcpyAsync(h->host_sc, &h->gs->rr, sizeof(double), cudaMemcpyDeviceToHost, s));
+            // every buffer of the iteration belongs to the handle, so its launches form a
+            // fixed sequence per slot j
+            auto body = [&](cudaStream_t q) -> mg_status {
+                TRY(applyP(h->r, z, q));
+                TRY(applyAS(z, w, j, q));
+                TRY(dispatch_j<RunOrth>(j, h, n, q));
+                CK(cudaMemcpyAsync(h->host_sc, &h->gs->rr, sizeof(double), cudaMemcpyDeviceToHost, q));
+                return MG_OK;
+            };
+            cudaGraphExec_t& ge = h->gexec[sys][j];
+            if (!ge && !h->prof && !h->graphs_off) capture_graph(h, body, &ge);
+            if (ge && !h->prof) CK(cudaGraphLaunch(ge, s));
+            else TRY(body(s));
             CK(cudaStreamSynchronize(s));
             ++it;
             const double rr = h->host_sc[0];
@@ -777,6 +810,7 @@ mg_status setup_impl(mg_handle* h, const mg_mesh* mesh, const mg_params* prm, co
     CK(cudaMemset(h->tickets, 0, TK_COUNT * sizeof(unsigned int)));
     CK(cudaMemset(h->gs, 0, sizeof(mg::GcrScal)));
     if (cudaMallocHost(&h->host_sc, 4 * sizeof(double)) != cudaSuccess) return MG_ERR_NOMEM;
+    CK(cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking));
     CK(cudaEventCreate(&h->ev0));
     CK(cudaEventCreate(&h->ev1));
     CK(cudaDeviceSynchronize());
@@ -787,6 +821,10 @@ void free_handle(mg_handle* h) {
     if (!h) return;
     for (void* p : h->allocs) cudaFree(p);
     if (h->host_sc) cudaFreeHost(h->host_sc);
+    for (auto& row : h->gexec)
+        for (cudaGraphExec_t g : row)
+            if (g) cudaGraphExecDestroy(g);
+    if (h->cap) cudaStreamDestroy(h->cap);
     if (h->ev0) cudaEventDestroy(h->ev0);
     if (h->ev1) cudaEventDestroy(h->ev1);
     for (cudaEvent_t e : h->evpool) cudaEventDestroy(e);
@@ -871,9 +909,9 @@ mg_status pressure_solve(mg_handle* h, const double* b, double* x, double tol, m
     if (!h || !b || !x || b == x || !(tol >= 0.0)) return MG_ERR_ARG;
     DeviceGuard dg(h->device);
     cudaStream_t s = S(stream);
-    auto A = [&](const double* z, double* w, int j) { return apply_gcr(h, z, w, j, s); };
-    auto P = [&](const double* r, double* z) { return run_vcycle(h, r, z, s); };
-    return gcr(h, cells(h, 0), b, x, tol, info, s, A, P);
+    auto A = [&](const double* z, double* w, int j, cudaStream_t q) { return apply_gcr(h, z, w, j, q); };
+    auto P = [&](const double* r, double* z, cudaStream_t q) { return run_vcycle(h, r, z, q); };
+    return gcr(h, 0, cells(h, 0), b, x, tol, info, s, A, P);
 }
 
 mg_status mixed_solve(mg_handle* h, const double* rhs_u, const double* rhs_p, double* u, double* p, double tol,
@@ -886,12 +924,12 @@ mg_status mixed_solve(mg_handle* h, const double* rhs_u, const double* rhs_p, do
     // GCR runs on concatenated [u; p] vectors held by the handle
     CK(cudaMemcpyAsync(h->mb, rhs_u, nu * sizeof(double), cudaMemcpyDeviceToDevice, s));
     CK(cudaMemcpyAsync(h->mb + nu, rhs_p, np * sizeof(double), cudaMemcpyDeviceToDevice, s));
-    auto A = [&](const double* v, double* y, int j) {
-        TRY(mixed_apply_impl(h, v, v + nu, y, y + nu, s));
-        return gcr_sums(h, n, y, j, s);
+    auto A = [&](const double* v, double* y, int j, cudaStream_t q) {
+        TRY(mixed_apply_impl(h, v, v + nu, y, y + nu, q));
+        return gcr_sums(h, n, y, j, q);
     };
-    auto P = [&](const double* r, double* z) { return schur_impl(h, r, r + nu, z, z + nu, s); };
-    const mg_status st = gcr(h, n, h->mb, h->mx, tol, info, s, A, P);
+    auto P = [&](const double* r, double* z, cudaStream_t q) { return schur_impl(h, r, r + nu, z, z + nu, q); };
+    const mg_status st = gcr(h, 1, n, h->mb, h->mx, tol, info, s, A, P);
     if (st == MG_OK || st == MG_ERR_NOT_CONVERGED || st == MG_ERR_BREAKDOWN) {
         CK(cudaMemcpyAsync(u, h->mx, nu * sizeof(double), cudaMemcpyDeviceToDevice, s));
         CK(cudaMemcpyAsync(p, h->mx + nu, np * sizeof(double), cudaMemcpyDeviceToDevice, s));
