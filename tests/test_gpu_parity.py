@@ -263,6 +263,24 @@ def test_repeat_calls_are_bitwise_deterministic(mg):
     assert np.array_equal(outs[0], outs[1]) and np.array_equal(outs[1], outs[2])
 
 
+def test_graph_replay_matches_direct_launches(mg):
+    """GCR iterations run from captured CUDA graphs after the first solve on a handle, and
+    as direct launches while per-launch profiling is on: both give bitwise the same x."""
+    cfg, inp, hier = problem("c20l9")
+    h = mg.mg_setup_config(cfg, inp, precision="fp32")
+    b = dev(inp["rhs"])
+    x1 = torch.zeros_like(b)
+    mg.pressure_solve(h, b, x1, tol=1e-9)          # captures the graphs
+    x2 = torch.zeros_like(b)
+    i2 = mg.pressure_solve(h, b, x2, tol=1e-9)     # replays them
+    mg.mg_profile_start(h, 1 << 14)
+    x3 = torch.zeros_like(b)
+    i3 = mg.pressure_solve(h, b, x3, tol=1e-9)     # direct launches
+    recs = mg.mg_profile_stop(h)
+    assert len(recs) > 0 and i2.iters == i3.iters
+    assert torch.equal(x1, x2) and torch.equal(x2, x3)
+
+
 # ---------------------------------------------------------------------------------------
 # mixed (u, p) system
 
