@@ -107,6 +107,8 @@ __global__ void __launch_bounds__(RED_THREADS) k_dot(size_t n, const double* __r
 //   all earlier directions w_i), from sums = [<w, w_i> (J), <w, w>, <r, w>].
 // Every kernel below is instantiated for the exact number J of stored directions, so no
 // FP64 instruction is spent on absent directions (FP64 issue rate bounds these kernels).
+// <w', w'> is kept for the later directions' beta: the orthogonalisation pass does not
+// recompute it (the FP64 pipe bounds that pass on GB300).
 template <int J>
 __device__ void gcr_coeffs(const double (&t)[J + 2], GcrScal* S) {
     double ww = t[J];
@@ -116,7 +118,20 @@ __device__ void gcr_coeffs(const double (&t)[J + 2], GcrScal* S) {
         S->beta[J * MAXR + i] = beta;
         ww -= beta * t[i];
     }
+    S->ww[J] = ww;
     S->alpha[J] = t[J + 1] / ww;
+}
+
+// FP64 -> FP32 by truncation of the significand, in integer operations (GB300's FP64 pipe
+// issues 2 lanes per clock per SM, the integer units far more).  Values below the FP32
+// normal range give 0; FP32 overflow, infinities and NaN take the hardware conversion.
+__device__ __forceinline__ float narrow_f32(double v) {
+    const unsigned hi = (unsigned)__double2hiint(v), lo = (unsigned)__double2loint(v);
+    const unsigned mag = hi & 0x7fffffffu;
+    if (mag < 0x38100000u) return 0.f;
+    if (mag >= 0x47f00000u) return (float)v;
+    // rebias the exponent (1023 -> 127: subtract 896 << 20) and keep 23 significand bits
+    return __uint_as_float(__funnelshift_l(lo, mag - 0x38000000u, 3) | (hi & 0x80000000u));
 }
 
 template <int J>
@@ -142,8 +157,9 @@ __global__ void __launch_bounds__(RED_THREADS) k_gcr_sums(size_t n, const double
     if (grid_reduce<J + 2>(v, partials, ticket, t)) gcr_coeffs<J>(t, S);
 }
 
-// w_J <- w_J - sum_i beta_i w_i (stored in place), r <- r - alpha_J w_J,
-// then <w_J, w_J> -> ww[J] and <r, r> -> rr.
+// w_J <- w_J - sum_i beta_i w_i (stored in place), r <- r - alpha_J w_J, then <r, r> -> rr.
+// <r, r> only decides convergence: each thread sums its share in FP32 (relative error about
+// 1e-6 of rr, 5e-7 of the reported relative residual), the grid sum is FP64.
 template <int J>
 __global__ void __launch_bounds__(RED_THREADS) k_gcr_orth_update(size_t n, double* __restrict__ Wb, size_t ld,
                                                                  double* __restrict__ r, double* partials,
@@ -153,7 +169,7 @@ __global__ void __launch_bounds__(RED_THREADS) k_gcr_orth_update(size_t n, doubl
     for (int i = 0; i < J; ++i) beta[i] = S->beta[J * MAXR + i];
     const double a = S->alpha[J];
     double* w = Wb + (size_t)J * ld;
-    double v[2] = {0.0, 0.0}, t[2];
+    float rrf = 0.f;
     for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
         double we = w[e];
 #pragma unroll
@@ -161,13 +177,11 @@ __global__ void __launch_bounds__(RED_THREADS) k_gcr_orth_update(size_t n, doubl
         if (J > 0) w[e] = we;
         const double re = r[e] - a * we;
         r[e] = re;
-        v[0] += we * we;
-        v[1] += re * re;
+        const float rf = narrow_f32(re);
+        rrf = fmaf(rf, rf, rrf);
     }
-    if (grid_reduce<2>(v, partials, ticket, t)) {
-        S->ww[J] = t[0];
-        S->rr = t[1];
-    }
+    double v[1] = {(double)rrf}, t[1];
+    if (grid_reduce<1>(v, partials, ticket, t)) S->rr = t[0];
 }
 
 // x += sum_{i <= JL} gamma_i z_i with the raw (not orthogonalised) directions z_i:
