@@ -123,6 +123,23 @@ class Clocks:
                            "samples": len(sm)}
 
 
+def max_over_ranks(x: float, pg, device: str) -> float:
+    """The maximum of x over all ranks (x itself without a process group): the job's time is
+    the slowest replica's."""
+    if pg is None:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    pg.all_reduce(t, op=pg.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_ms_per_unit(ms_max: float, units_per_rank: int, world: int) -> float:
+    """Whole-job time per unit: every rank solves `units_per_rank` independent problems (weak
+    scaling, replicas), so the job processes units_per_rank * world of them in ms_max."""
+    return ms_max / (units_per_rank * world)
+
+
 def dist_init():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -196,6 +213,65 @@ def run_reference(args, cfg, inp, world, rank):
     print(json.dumps(line), flush=True)
 
 
+def run_mixed(args, cfg, inp, mg, torch, world, rank):
+    """The mixed (u, p) solve: GCR(5) on the reduced mixed operator, right-preconditioned by the
+    Schur-complement step with one V-cycle (Sec. 3.4, 4.1), from zero to 1e-8."""
+    h = mg.mg_setup_config(cfg, inp, precision=args.precision, mixed=True)
+    ru = torch.from_numpy(inp["rhs_u"]).cuda()
+    rp = torch.from_numpy(inp["rhs_p"]).cuda()
+    u, p = torch.zeros_like(ru), torch.zeros_like(rp)
+    for _ in range(args.warmup):
+        info = mg.mixed_solve(h, ru, rp, u, p, tol=args.tol)
+        assert info.converged, info
+    # untimed: every launch of a few solves
+    n_prof = 3
+    mg.mg_profile_start(h, 1 << 16)
+    for _ in range(n_prof):
+        mg.mixed_solve(h, ru, rp, u, p, tol=args.tol)
+    recs = mg.mg_profile_stop(h)
+    by = {}
+    for r in recs:
+        a = by.setdefault((r["kind"], r["level"]), [0, 0.0, 0.0])
+        a[0] += 1
+        a[1] += r["ms"]
+        a[2] += r["bytes"]
+    total = sum(v[1] for v in by.values())
+    (kind, lev), (cnt, ms, byt) = max(by.items(), key=lambda kv: kv[1][1])
+    peak, peak_src = _peaks()
+    # timed region
+    torch.cuda.synchronize()
+    iters = []
+    with Clocks(0) as clk:
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(args.steps):
+            info = mg.mixed_solve(h, ru, rp, u, p, tol=args.tol)
+            iters.append(info.iters)
+        e1.record()
+        torch.cuda.synchronize()
+    ms_solve = e0.elapsed_time(e1) / args.steps
+    line = {
+        "metric": f"ms per mixed (u, p) solve to {args.tol:g} rel. residual at {cfg.name.upper()}",
+        "value": round(ms_solve, 4), "unit": "ms", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "higher_is_better": False, "dtype": "f64" if args.precision == "fp64" else "f64+f32", "data": "synthetic",
+        "config": {"workload": f"{cfg.name} mixed system (eps = {cfg.eps}), GCR(5) + Schur-complement "
+                               f"{cfg.levels}-level {args.precision} V-cycle", "n": cfg.n, "nlev": cfg.nlev,
+                   "unknowns_u": int(ru.numel()), "unknowns_p": int(rp.numel()),
+                   "iters_per_solve": statistics.mean(iters)},
+        "roofline": {"bound": "hbm", "kernel": f"{kind}@L{lev}", "achieved": round(byt / (ms * 1e-3) / 1e9, 1),
+                     "peak": peak, "unit": "GB/s", "frac": round(byt / (ms * 1e-3) / 1e9 / peak, 4),
+                     "peak_source": peak_src, "timing": f"CUDA events around every launch of {n_prof} untimed solves"},
+        "kernels": {f"{k[0]}@L{k[1]}": {"launches": v[0] // n_prof, "ms": round(v[1] / n_prof, 4),
+                                        "share": round(v[1] / total, 4),
+                                        "GBps": round(v[2] / (v[1] * 1e-3) / 1e9, 1)}
+                    for k, v in sorted(by.items(), key=lambda kv: -kv[1][1])},
+        "clocks": clk.result,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    h.destroy()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -204,6 +280,9 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="c192")
     ap.add_argument("--precision", default="fp32", choices=["fp64", "fp32", "fp32_bf16"])
+    ap.add_argument("--system", default="pressure", choices=["pressure", "mixed"],
+                    help="mixed: the (u, p) solve (GCR + Schur-complement multigrid) on the C48L30 "
+                         "mixed workload instead of the headline pressure solve")
     ap.add_argument("--tol", type=float, default=1e-8)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--profile-solve", action="store_true",
@@ -213,8 +292,15 @@ def main():
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3
     world, rank, local = dist_init()
+    if args.system == "mixed" and args.workload == "c192":
+        args.workload = "c48"
     cfg = syn.config(args.workload)
-    inp = syn.make_inputs(cfg, mixed=False)
+    inp = syn.make_inputs(cfg, mixed=args.system == "mixed")
+    if args.impl == "reference" and args.system == "mixed":
+        if rank == 0:
+            print(json.dumps({"impl": "reference", "unavailable": "the reference arm times the pressure solve "
+                                                                  "only (the headline metric)"}))
+        return
     if args.impl == "reference":
         return run_reference(args, cfg, inp, world, rank)
 
@@ -231,6 +317,9 @@ def main():
     if pg:
         pg.barrier()
     import paper_2002_00756_gb300 as mg
+
+    if args.system == "mixed":
+        return run_mixed(args, cfg, inp, mg, torch, world, rank)
 
     if args.profile_solve:
         h = mg.mg_setup_config(cfg, inp, precision=args.precision, mixed=False, max_iter=args.iters)
@@ -280,12 +369,8 @@ def main():
         torch.cuda.synchronize()
         if pg:
             pg.barrier()
-    ms_total = e0.elapsed_time(e1)
-    if pg:
-        t = torch.tensor([ms_total], device="cuda")
-        pg.all_reduce(t, op=pg.ReduceOp.MAX)
-        ms_total = float(t.item())
-    ms_per_solve = ms_total / (args.steps * world)
+    ms_total = max_over_ranks(e0.elapsed_time(e1), pg, "cuda")
+    ms_per_solve = job_ms_per_unit(ms_total, args.steps, world)
 
     # ---- e2e: host buffers through the public API ----
     bh = torch.from_numpy(inp["rhs"]).pin_memory()
@@ -302,12 +387,7 @@ def main():
         mg.pressure_solve(h, bd, xd, tol=args.tol)
         xh.copy_(xd, non_blocking=True)
         torch.cuda.synchronize()
-    e2e_ms = (time.perf_counter() - t0) * 1e3
-    if pg:
-        t = torch.tensor([e2e_ms], device="cuda")
-        pg.all_reduce(t, op=pg.ReduceOp.MAX)
-        e2e_ms = float(t.item())
-    e2e_ms /= (e2e_steps * world)
+    e2e_ms = job_ms_per_unit(max_over_ranks((time.perf_counter() - t0) * 1e3, pg, "cuda"), e2e_steps, world)
 
     # ---- roofline of the dominant kernel: K more solves, timed the same way, with CUDA
     # events around every launch of the dominant kernel's kind and level (the solves then
