@@ -154,14 +154,21 @@ struct SweepShal {
 #ifndef MG_SWEEP_BLOCK
 #define MG_SWEEP_BLOCK 128
 #endif
+#ifndef MG_SWEEP_BF16_PAIRS
+#define MG_SWEEP_BF16_PAIRS 1
+#endif
 template <typename T, typename C, int MODE, typename X, typename B, typename O, bool BCOPY, int DEEP, int SHAL>
 __global__ void __launch_bounds__(MG_SWEEP_BLOCK, 4) k_sweep(Lvl<T, C> L, const X* __restrict__ x, const T* __restrict__ xc,
                         int ncol_c, const B* __restrict__ b, T* __restrict__ bcopy,
                         O* __restrict__ xo, T omega) {
     static_assert(DEEP % SHAL == 0, "ring lengths");
     static_assert(sizeof(X) == sizeof(T), "iterate type");
-    // asynchronous copies move 4, 8 or 16 bytes: BF16 coefficients use the register ring
-    constexpr bool ASYNC_C = sizeof(C) >= 4;
+    // asynchronous copies move 4, 8 or 16 bytes: a BF16 coefficient travels in the aligned
+    // 4-byte pair that holds it (its neighbour in memory rides along) and is picked out of
+    // the pair in the ring
+    constexpr bool PAIR = sizeof(C) == 2;
+    constexpr bool ASYNC_C = sizeof(C) >= 4 || (PAIR && MG_SWEEP_BF16_PAIRS);
+    typedef typename std::conditional<PAIR, uint32_t, C>::type CW;   // ring word of a coefficient
     constexpr bool PRO = (MODE == XM_PROLONG || MODE == XM_PROLONG0);
     constexpr bool RAW = (MODE == XM_PLAIN || MODE == XM_PROLONG);   // reads the fine iterate
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -171,9 +178,9 @@ __global__ void __launch_bounds__(MG_SWEEP_BLOCK, 4) k_sweep(Lvl<T, C> L, const 
     // [stash 2 x hsteps (T)] [1/dz, nlev (T)]
     B* rb = reinterpret_cast<B*>(smem_raw);
     T* rx = reinterpret_cast<T*>(rb + (size_t)DEEP * bd);
-    C* rte = reinterpret_cast<C*>(rx + (size_t)DEEP * bd);
-    C* rtn = rte + (size_t)DEEP * bd;
-    C* rtv = rtn + (size_t)DEEP * bd;
+    CW* rte = reinterpret_cast<CW*>(rx + (size_t)DEEP * bd);
+    CW* rtn = rte + (size_t)DEEP * bd;
+    CW* rtv = rtn + (size_t)DEEP * bd;
     T* sc = reinterpret_cast<T*>(ASYNC_C ? (unsigned char*)(rtv + (size_t)DEEP * bd)
                                          : (unsigned char*)rte);
     T* se = sc + (size_t)hsteps * bd;
@@ -219,6 +226,12 @@ __global__ void __launch_bounds__(MG_SWEEP_BLOCK, 4) k_sweep(Lvl<T, C> L, const 
     const C* ptv = L.Tv + c + (upper ? 0u : ncol);
     const T* pch[4] = {xc + pn[0], xc + pn[1], xc + pn[2], xc + pn[3]};
     const T* pcc = xc + pc;
+    // BF16 pairs: word bases (offsets in words: kc for the faces, whose level holds 2 ncol
+    // values, kc / 2 for the vertical faces) and the half of the word that holds the value
+    const uint32_t* pte2 = reinterpret_cast<const uint32_t*>(L.Th) + (fo[0] >> 1);
+    const uint32_t* ptn2 = reinterpret_cast<const uint32_t*>(L.Th) + (fo[2] >> 1);
+    const uint32_t* ptv2 = reinterpret_cast<const uint32_t*>(L.Tv) + ((c + (upper ? 0u : ncol)) >> 1);
+    auto half = [](uint32_t w, int h) -> T { return (T)__uint_as_float(h ? (w & 0xffff0000u) : (w << 16)); };
 
     auto stage = [&](int i, int slot, unsigned kc, bool chk) {
         if (!chk || i < nsteps) {
@@ -228,7 +241,11 @@ __global__ void __launch_bounds__(MG_SWEEP_BLOCK, 4) k_sweep(Lvl<T, C> L, const 
                 const bool in = !chk || i + 1 < nsteps || (upper ? kfirst - i - 1 >= 0 : kfirst + i + 1 < nlev);
                 __pipeline_memcpy_async(rx + so, px + (in ? kc + dkc : kc), sizeof(T), in ? 0 : sizeof(T));
             }
-            if (ASYNC_C) {
+            if (ASYNC_C && PAIR) {
+                __pipeline_memcpy_async(rte + so, pte2 + kc, 4);
+                __pipeline_memcpy_async(rtn + so, ptn2 + kc, 4);
+                __pipeline_memcpy_async(rtv + so, ptv2 + (kc >> 1), 4);
+            } else if (ASYNC_C) {
                 __pipeline_memcpy_async(rte + so, pth[0] + 2 * kc, sizeof(C));
                 __pipeline_memcpy_async(rtn + so, pth[2] + 2 * kc, sizeof(C));
                 __pipeline_memcpy_async(rtv + so, ptv + kc, sizeof(C));
@@ -290,10 +307,17 @@ __global__ void __launch_bounds__(MG_SWEEP_BLOCK, 4) k_sweep(Lvl<T, C> L, const 
         T xn = RAW ? rx[so] : T(0);
         T te = T(0), tn = T(0), tv = T(0), twl = T(0);
         if (ASYNC_C) {
-            te = (T)rte[so];
-            tn = (T)rtn[so];
-            tv = (T)rtv[so];
-            if (shWf) twl = (T)rte[so - 1];
+            if constexpr (PAIR) {
+                te = half(rte[so], fo[0] & 1);
+                tn = half(rtn[so], fo[2] & 1);
+                tv = half(rtv[so], c & 1);
+                if (shWf) twl = half(rte[so - 1], fo[1] & 1);
+            } else {
+                te = (T)rte[so];
+                tn = (T)rtn[so];
+                tv = (T)rtv[so];
+                if (shWf) twl = (T)rte[so - 1];
+            }
         }
         __syncwarp();   // reads of the slot are done before it is refilled
         stage(i + DEEP, j, kc_st, chk);

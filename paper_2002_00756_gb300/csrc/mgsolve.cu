@@ -277,8 +277,10 @@ mg_status launch_sweep(mg_handle* h, int lev, const Lvl<T, C>& L, const X* x, co
     // stash (2 values per step of half a column); it must fit the budget
     constexpr int DEEP = SweepPF<T>::deep;
     const int hsteps = (L.nlev + 1) / 2;
-    const size_t per_thread = DEEP * (sizeof(B) + sizeof(T) + (sizeof(C) >= 4 ? 3 * sizeof(C) : 0)) +
-                              2 * (size_t)hsteps * sizeof(T);
+    // (BF16 coefficients travel as 4-byte pairs)
+    const size_t per_thread =
+        DEEP * (sizeof(B) + sizeof(T) + (sizeof(C) >= 4 ? 3 * sizeof(C) : (MG_SWEEP_BF16_PAIRS ? 12 : 0))) +
+        2 * (size_t)hsteps * sizeof(T);
     const size_t per_block = (size_t)L.nlev * sizeof(T);   // the 1/dz table
     int bd = sweep_block(2 * L.ncol);
     const int cap = (int)((SWEEP_SMEM_MAX - per_block) / per_thread) / 32 * 32;
