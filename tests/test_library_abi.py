@@ -70,6 +70,12 @@ def test_setup_rejects_bad_arguments_on_the_host(lib, kw):
     assert st == -1 and not out.value
 
 
+def test_setup_rejects_meshes_beyond_32_bit_level_offsets(lib):
+    # 2 (nlev + 1) 6 n^2 >= 2^32: refused before any device work (no GPU needed)
+    st, out = _setup_raw(lib, n=2400, nlev=70, levels=1, g=np.ones(1))
+    assert st == -7 and not out.value
+
+
 def test_setup_rejects_non_positive_factors(lib):
     g = np.ones(6 * 16 * 3)
     g[5] = -1.0
