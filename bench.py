@@ -123,6 +123,18 @@ class Clocks:
                            "samples": len(sm)}
 
 
+def workload_name(cfg, precision: str) -> str:
+    """The headline workload's name, with what differs from it spelled out."""
+    name = WORKLOAD if precision == "fp32" else WORKLOAD.replace("FP32", precision)
+    if cfg.levels != 4:
+        name = name.replace("4-level", f"{cfg.levels}-level")
+    if cfg.dt != 600.0:
+        name += f", dt {cfg.dt:g} s"
+    if cfg.name != "c192":
+        name = name.replace("C192L70", f"C{cfg.n}L{cfg.nlev}")
+    return name
+
+
 def max_over_ranks(x: float, pg, device: str) -> float:
     """The maximum of x over all ranks (x itself without a process group): the job's time is
     the slowest replica's."""
@@ -280,6 +292,10 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="c192")
     ap.add_argument("--precision", default="fp32", choices=["fp64", "fp32", "fp32_bf16"])
+    ap.add_argument("--dt", type=float, default=None,
+                    help="time step in s (default: the workload's, 600 s; 1200 s gives CFL_h ~ 7.9 at C192, "
+                         "the paper's regime for the robustness sweep)")
+    ap.add_argument("--levels", type=int, default=None, help="multigrid levels (default: the workload's)")
     ap.add_argument("--system", default="pressure", choices=["pressure", "mixed"],
                     help="mixed: the (u, p) solve (GCR + Schur-complement multigrid) on the C48L30 "
                          "mixed workload instead of the headline pressure solve")
@@ -295,6 +311,9 @@ def main():
     if args.system == "mixed" and args.workload == "c192":
         args.workload = "c48"
     cfg = syn.config(args.workload)
+    if args.dt is not None or args.levels is not None:
+        import dataclasses
+        cfg = dataclasses.replace(cfg, dt=args.dt or cfg.dt, levels=args.levels or cfg.levels)
     inp = syn.make_inputs(cfg, mixed=args.system == "mixed")
     if args.impl == "reference" and args.system == "mixed":
         if rank == 0:
@@ -431,8 +450,8 @@ def main():
         "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
         "dtype": "f64" if args.precision == "fp64" else "f64+f32",
         "data": "synthetic",
-        "config": {"workload": WORKLOAD if args.precision == "fp32" else WORKLOAD.replace("FP32", args.precision),
-                   "n": cfg.n, "nlev": cfg.nlev, "unknowns": cfg.ncell, "levels": cfg.levels,
+        "config": {"workload": workload_name(cfg, args.precision),
+                   "n": cfg.n, "nlev": cfg.nlev, "unknowns": cfg.ncell, "levels": cfg.levels, "dt_s": cfg.dt,
                    "vcycle_precision": args.precision, "tol": args.tol, "gcr_restart": cfg.gcr_restart,
                    "iters_per_solve": statistics.mean(iters), "replicas": world,
                    "l2": "working set (~3 GB) larger than L2; no flush"},
