@@ -225,6 +225,64 @@ def run_reference(args, cfg, inp, world, rank):
     print(json.dumps(line), flush=True)
 
 
+ENSEMBLE = [(n, nlev) for n in (32, 40, 48, 64, 80, 96, 112, 128) for nlev in (30, 50, 70)]
+
+
+def run_ensemble(args, mg, torch, world, rank):
+    """24 independent pressure solves (C32-C128 x 30 / 50 / 70 levels, 4-level FP32 V-cycle,
+    GCR(5) FP64, tol 1e-8), solved one after the other through pressure_solve and together
+    through ensemble_pressure_solve (interleaved iterations, one stream per member)."""
+    hs, bs, xs = [], [], []
+    for i, (n, nlev) in enumerate(ENSEMBLE):
+        cfg = syn.small_config(n, nlev, levels=4, seed=syn.BASE_SEED + 200 + i)
+        inp = syn.make_inputs(cfg, mixed=False)
+        hs.append(mg.mg_setup_config(cfg, inp, precision=args.precision, mixed=False))
+        bs.append(torch.from_numpy(inp["rhs"]).cuda())
+        xs.append(torch.zeros_like(bs[-1]))
+    cells = sum(int(b.numel()) for b in bs)
+    for _ in range(args.warmup):
+        for h, b, x in zip(hs, bs, xs):
+            mg.pressure_solve(h, b, x, tol=args.tol)
+        mg.ensemble_pressure_solve(hs, bs, xs, tol=args.tol)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with Clocks(0) as clk:
+        e0.record()
+        for _ in range(args.steps):
+            for h, b, x in zip(hs, bs, xs):
+                mg.pressure_solve(h, b, x, tol=args.tol)
+        e1.record()
+        torch.cuda.synchronize()
+        seq_ms = e0.elapsed_time(e1) / args.steps
+        lat = []
+        e0.record()
+        for _ in range(args.steps):
+            infos = mg.ensemble_pressure_solve(hs, bs, xs, tol=args.tol)
+            lat += [i.ms for i in infos]
+            assert all(i.converged for i in infos), infos
+        e1.record()
+        torch.cuda.synchronize()
+        ens_ms = e0.elapsed_time(e1) / args.steps
+    lat = np.sort(np.array(lat))
+    line = {
+        "metric": "members per second, 24-member pressure-solve ensemble (C32-C128 x 30/50/70 levels)",
+        "value": round(len(hs) / (ens_ms * 1e-3), 2), "unit": "members/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(ens_ms, 3), "higher_is_better": True,
+        "dtype": "f64" if args.precision == "fp64" else "f64+f32", "data": "synthetic",
+        "config": {"workload": f"24 members, n in (32..128), nlev in (30, 50, 70), 4-level {args.precision} "
+                               f"V-cycle, GCR(5), tol {args.tol:g}", "cells": cells, "members": len(hs)},
+        "sequential": {"members_per_s": round(len(hs) / (seq_ms * 1e-3), 2), "ms": round(seq_ms, 3)},
+        "speedup_vs_sequential": round(seq_ms / ens_ms, 3),
+        "member_latency_ms": {"p50": round(float(np.percentile(lat, 50)), 3),
+                              "p99": round(float(np.percentile(lat, 99)), 3), "max": round(float(lat[-1]), 3)},
+        "clocks": clk.result,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    for h in hs:
+        h.destroy()
+
+
 def run_mixed(args, cfg, inp, mg, torch, world, rank):
     """The mixed (u, p) solve: GCR(5) on the reduced mixed operator, right-preconditioned by the
     Schur-complement step with one V-cycle (Sec. 3.4, 4.1), from zero to 1e-8."""
@@ -296,7 +354,7 @@ def main():
                     help="time step in s (default: the workload's, 600 s; 1200 s gives CFL_h ~ 7.9 at C192, "
                          "the paper's regime for the robustness sweep)")
     ap.add_argument("--levels", type=int, default=None, help="multigrid levels (default: the workload's)")
-    ap.add_argument("--system", default="pressure", choices=["pressure", "mixed"],
+    ap.add_argument("--system", default="pressure", choices=["pressure", "mixed", "ensemble"],
                     help="mixed: the (u, p) solve (GCR + Schur-complement multigrid) on the C48L30 "
                          "mixed workload instead of the headline pressure solve")
     ap.add_argument("--tol", type=float, default=1e-8)
@@ -310,6 +368,11 @@ def main():
     world, rank, local = dist_init()
     if args.system == "mixed" and args.workload == "c192":
         args.workload = "c48"
+    if args.impl == "reference" and args.system == "ensemble":
+        if rank == 0:
+            print(json.dumps({"impl": "reference", "unavailable": "the reference arm times the pressure solve "
+                                                                  "only (the headline metric)"}))
+        return
     cfg = syn.config(args.workload)
     if args.dt is not None or args.levels is not None:
         import dataclasses
@@ -339,6 +402,8 @@ def main():
 
     if args.system == "mixed":
         return run_mixed(args, cfg, inp, mg, torch, world, rank)
+    if args.system == "ensemble":
+        return run_ensemble(args, mg, torch, world, rank)
 
     if args.profile_solve:
         h = mg.mg_setup_config(cfg, inp, precision=args.precision, mixed=False, max_iter=args.iters)

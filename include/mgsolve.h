@@ -178,6 +178,25 @@ mg_status mg_residual_restrict(mg_handle* h, int32_t level, const double* b, con
 /* x += Prolongate(xc) from level+1 onto level (Eq. prolongation, natural injection). */
 mg_status mg_prolong_add(mg_handle* h, int32_t level, const double* xc, double* x, void* stream);
 
+/* Ensemble of independent pressure solves (the batched-ensemble use of Sec. 4.1's solver:
+ * many members, each its own mesh, levels and precision): handles[i] solves
+ * H_i x[i] = b[i] exactly as pressure_solve does (same kernels in the same order, so the
+ * same x bit for bit), and the members' iterations are interleaved: each round launches one
+ * GCR iteration of every unfinished member on that member's own stream, so small members run
+ * side by side on the GPU, then the host reads their residual norms.
+ *   handles   count distinct handles of one device
+ *   b, x      count DEVICE pointers each, N_i doubles (x[i] != b[i])
+ *   infos     NULL or count entries: iterations, final relative residual, and the member's
+ *             time from its first launch to its last on the GPU [ms]
+ *   statuses  NULL or count entries: each member's status (as pressure_solve returns it)
+ *   stream    the members start after the work queued on this stream so far
+ * Synchronous: returns when every member is done.  Returns MG_OK if every member converged,
+ * else the first member's non-OK status; MG_ERR_ARG for a NULL or repeated handle, handles
+ * on different devices, or x[i] == b[i]. */
+mg_status ensemble_pressure_solve(mg_handle* const* handles, int32_t count, const double* const* b,
+                                  double* const* x, double tol, mg_solve_info* infos, int32_t* statuses,
+                                  void* stream);
+
 /* [yu; yp] = A [u; p], the mixed operator (needs mixed data). */
 mg_status mixed_apply(mg_handle* h, const double* u, const double* p, double* yu, double* yp,
                       void* stream);

@@ -71,6 +71,8 @@ _SIGS = {
     "helmholtz_apply": [_VP, _DP, _DP, _VP],
     "vcycle": [_VP, _DP, _DP, _VP],
     "pressure_solve": [_VP, _DP, _DP, _D, ctypes.POINTER(_Info), _VP],
+    "ensemble_pressure_solve": [_VP, _I32, _VP, _VP, _D, ctypes.POINTER(_Info), ctypes.POINTER(ctypes.c_int32),
+                                _VP],
     "mixed_solve": [_VP, _DP, _DP, _DP, _DP, _D, ctypes.POINTER(_Info), _VP],
     "mg_level_apply": [_VP, _I32, _DP, _DP, _VP],
     "mg_smooth": [_VP, _I32, _DP, _DP, _DP, _I32, _VP],
@@ -248,6 +250,23 @@ def pressure_solve(h: Handle, b, x, tol: float = 1e-8, stream=None) -> SolveInfo
     st = load().pressure_solve(h.ptr, _ptr(b, h.ncell, "b"), _ptr(x, h.ncell, "x"), tol, ctypes.byref(info),
                                _stream(stream))
     return _solve_status(st, info, "pressure_solve")
+
+
+def ensemble_pressure_solve(handles, bs, xs, tol: float = 1e-8, stream=None) -> list[SolveInfo]:
+    """Independent pressure solves, one per handle, with interleaved iterations (see
+    ensemble_pressure_solve in mgsolve.h); returns each member's SolveInfo."""
+    n = len(handles)
+    if len(bs) != n or len(xs) != n:
+        raise ValueError("one b and one x per handle")
+    hs = (ctypes.c_void_p * n)(*[h.ptr for h in handles])
+    bp = (ctypes.c_void_p * n)(*[_ptr(b, h.ncell, "b").value for b, h in zip(bs, handles)])
+    xp = (ctypes.c_void_p * n)(*[_ptr(x, h.ncell, "x").value for x, h in zip(xs, handles)])
+    infos = (_Info * max(n, 1))()
+    sts = (ctypes.c_int32 * max(n, 1))()
+    st = load().ensemble_pressure_solve(hs, n, bp, xp, tol, infos, sts, _stream(stream))
+    if st not in (MG_OK, MG_ERR_NOT_CONVERGED, MG_ERR_BREAKDOWN):
+        raise MGError(st, "ensemble_pressure_solve")
+    return [SolveInfo(sts[i], infos[i].iters, infos[i].rel_res, infos[i].ms) for i in range(n)]
 
 
 def mixed_solve(h: Handle, rhs_u, rhs_p, u, p, tol: float = 1e-8, stream=None) -> SolveInfo:

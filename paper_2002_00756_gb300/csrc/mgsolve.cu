@@ -96,6 +96,8 @@ struct mg_handle {
     // operator with its sums, the orthogonalisation and the read-back of <r, r>, captured on
     // `cap` the first time and replayed on the caller's stream afterwards
     cudaStream_t cap = nullptr;
+    cudaStream_t run = nullptr;   // the handle's stream inside an ensemble solve
+    cudaEvent_t evx = nullptr;    // ordering event (no timing)
     cudaGraphExec_t gexec[2][mg::MAXR] = {};
     bool graphs_off = false;
     int red_grid = 0;
@@ -524,72 +526,119 @@ void capture_graph(mg_handle* h, Body& body, cudaGraphExec_t* out) {
     }
 }
 
-template <typename ApplyAS, typename ApplyP>
-mg_status gcr(mg_handle* h, int sys, size_t n, const double* b, double* x, double tol, mg_solve_info* info,
-              cudaStream_t s, ApplyAS applyAS, ApplyP applyP) {
-    const int m = h->prm.gcr_restart;
-    const int G = h->red_grid;
+// One GCR solve as resumable steps, so that several solves (an ensemble of handles) can
+// interleave their iterations on their own streams: start (enqueue r = b, x = 0, <b, b>),
+// started (after a synchronisation: read <b, b>), launch (enqueue one iteration, ending with
+// the read-back of <r, r>), landed (after a synchronisation: read <r, r>, decide, enqueue the
+// solution update when the cycle ends or the solve stops), end (enqueue the closing event).
+struct GcrRun {
+    int sys = 0;          // 0 pressure, 1 mixed: selects the handle's cached graphs
+    size_t n = 0;
+    double* x = nullptr;
+    double tol = 0.0;
+    double bb = 0.0, rel = 0.0;
+    int it = 0;
+    mg_status st = MG_OK;
+    bool active = false;  // iterations left to launch
+};
+
+mg_status gcr_start(mg_handle* h, GcrRun& g, const double* b, cudaStream_t s) {
     CK(cudaEventRecord(h->ev0, s));
-    CK(cudaMemcpyAsync(h->r, b, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
-    CK(cudaMemsetAsync(x, 0, n * sizeof(double), s));
+    CK(cudaMemcpyAsync(h->r, b, g.n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    CK(cudaMemsetAsync(g.x, 0, g.n * sizeof(double), s));
     {
-        Prof pr(h, MG_K_DOT, 0, 8.0 * n, s);
-        mg::k_dot<<<G, mg::RED_THREADS, 0, s>>>(n, b, b, h->partials, h->tickets + TK_DOT, &h->gs->bb);
+        Prof pr(h, MG_K_DOT, 0, 8.0 * g.n, s);
+        mg::k_dot<<<h->red_grid, mg::RED_THREADS, 0, s>>>(g.n, b, b, h->partials, h->tickets + TK_DOT, &h->gs->bb);
         CK(cudaGetLastError());
     }
     CK(cudaMemcpyAsync(h->host_sc, &h->gs->bb, sizeof(double), cudaMemcpyDeviceToHost, s));
+    return MG_OK;
+}
+
+void gcr_started(mg_handle* h, GcrRun& g) {
+    g.bb = h->host_sc[0];
+    g.it = 0;
+    g.rel = 0.0;
+    g.active = false;
+    g.st = MG_OK;
+    if (!std::isfinite(g.bb)) {
+        g.st = MG_ERR_BREAKDOWN;
+    } else if (g.bb > 0.0) {
+        g.rel = 1.0;
+        g.st = MG_ERR_NOT_CONVERGED;
+        g.active = h->prm.max_iter > 0;
+    }
+}
+
+template <typename ApplyAS, typename ApplyP>
+mg_status gcr_launch(mg_handle* h, GcrRun& g, cudaStream_t s, ApplyAS& applyAS, ApplyP& applyP) {
+    const int j = g.it % h->prm.gcr_restart;
+    double* z = h->Z + (size_t)j * h->glen;
+    double* w = h->W + (size_t)j * h->glen;
+    const size_t n = g.n;
+    // every buffer of the iteration belongs to the handle, so its launches form a fixed
+    // sequence per slot j
+    auto body = [&](cudaStream_t q) -> mg_status {
+        TRY(applyP(h->r, z, q));
+        TRY(applyAS(z, w, j, q));
+        TRY(dispatch_j<RunOrth>(j, h, n, q));
+        CK(cudaMemcpyAsync(h->host_sc, &h->gs->rr, sizeof(double), cudaMemcpyDeviceToHost, q));
+        return MG_OK;
+    };
+    cudaGraphExec_t& ge = h->gexec[g.sys][j];
+    if (!ge && !h->prof && !h->graphs_off) capture_graph(h, body, &ge);
+    if (ge && !h->prof) CK(cudaGraphLaunch(ge, s));
+    else TRY(body(s));
+    return MG_OK;
+}
+
+mg_status gcr_landed(mg_handle* h, GcrRun& g, cudaStream_t s) {
+    const int j = g.it % h->prm.gcr_restart;
+    ++g.it;
+    const double rr = h->host_sc[0];
+    if (!std::isfinite(rr)) {
+        g.st = MG_ERR_BREAKDOWN;
+        g.active = false;
+        return MG_OK;
+    }
+    g.rel = std::sqrt(rr / g.bb);
+    const bool done = g.rel <= g.tol;
+    if (j == h->prm.gcr_restart - 1 || done || g.it == h->prm.max_iter)
+        TRY(dispatch_j<RunXupd>(j, h, g.n, g.x, s));
+    if (done) g.st = MG_OK;
+    g.active = !done && g.it < h->prm.max_iter;
+    return MG_OK;
+}
+
+void gcr_info(mg_handle* h, const GcrRun& g, mg_solve_info* info) {
+    if (!info) return;
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, h->ev0, h->ev1);
+    info->iters = g.it;
+    info->rel_res = g.rel;
+    info->ms = ms;
+}
+
+template <typename ApplyAS, typename ApplyP>
+mg_status gcr(mg_handle* h, int sys, size_t n, const double* b, double* x, double tol, mg_solve_info* info,
+              cudaStream_t s, ApplyAS applyAS, ApplyP applyP) {
+    GcrRun g;
+    g.sys = sys;
+    g.n = n;
+    g.x = x;
+    g.tol = tol;
+    TRY(gcr_start(h, g, b, s));
     CK(cudaStreamSynchronize(s));
-    const double bb = h->host_sc[0];
-    mg_status st = MG_OK;
-    int it = 0;
-    double rel = 0.0;
-    if (!std::isfinite(bb)) st = MG_ERR_BREAKDOWN;
-    else if (bb > 0.0) {
-        rel = 1.0;
-        st = MG_ERR_NOT_CONVERGED;
-        while (it < h->prm.max_iter) {
-            const int j = it % m;
-            double* z = h->Z + (size_t)j * h->glen;
-            double* w = h->W + (size_t)j * h->glen;
-            // every buffer of the iteration belongs to the handle, so its launches form a
-            // fixed sequence per slot j
-            auto body = [&](cudaStream_t q) -> mg_status {
-                TRY(applyP(h->r, z, q));
-                TRY(applyAS(z, w, j, q));
-                TRY(dispatch_j<RunOrth>(j, h, n, q));
-                CK(cudaMemcpyAsync(h->host_sc, &h->gs->rr, sizeof(double), cudaMemcpyDeviceToHost, q));
-                return MG_OK;
-            };
-            cudaGraphExec_t& ge = h->gexec[sys][j];
-            if (!ge && !h->prof && !h->graphs_off) capture_graph(h, body, &ge);
-            if (ge && !h->prof) CK(cudaGraphLaunch(ge, s));
-            else TRY(body(s));
-            CK(cudaStreamSynchronize(s));
-            ++it;
-            const double rr = h->host_sc[0];
-            if (!std::isfinite(rr)) {
-                st = MG_ERR_BREAKDOWN;
-                break;
-            }
-            rel = std::sqrt(rr / bb);
-            const bool done = rel <= tol;
-            if (j == m - 1 || done || it == h->prm.max_iter) TRY(dispatch_j<RunXupd>(j, h, n, x, s));
-            if (done) {
-                st = MG_OK;
-                break;
-            }
-        }
+    gcr_started(h, g);
+    while (g.active) {
+        TRY(gcr_launch(h, g, s, applyAS, applyP));
+        CK(cudaStreamSynchronize(s));
+        TRY(gcr_landed(h, g, s));
     }
     CK(cudaEventRecord(h->ev1, s));
     CK(cudaEventSynchronize(h->ev1));
-    if (info) {
-        float ms = 0.f;
-        cudaEventElapsedTime(&ms, h->ev0, h->ev1);
-        info->iters = it;
-        info->rel_res = rel;
-        info->ms = ms;
-    }
-    return st;
+    gcr_info(h, g, info);
+    return g.st;
 }
 
 // ---- mixed operator and Schur-complement preconditioner ----
@@ -813,6 +862,8 @@ mg_status setup_impl(mg_handle* h, const mg_mesh* mesh, const mg_params* prm, co
     CK(cudaMemset(h->gs, 0, sizeof(mg::GcrScal)));
     if (cudaMallocHost(&h->host_sc, 4 * sizeof(double)) != cudaSuccess) return MG_ERR_NOMEM;
     CK(cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking));
+    CK(cudaStreamCreateWithFlags(&h->run, cudaStreamNonBlocking));
+    CK(cudaEventCreateWithFlags(&h->evx, cudaEventDisableTiming));
     CK(cudaEventCreate(&h->ev0));
     CK(cudaEventCreate(&h->ev1));
     CK(cudaDeviceSynchronize());
@@ -827,6 +878,8 @@ void free_handle(mg_handle* h) {
         for (cudaGraphExec_t g : row)
             if (g) cudaGraphExecDestroy(g);
     if (h->cap) cudaStreamDestroy(h->cap);
+    if (h->run) cudaStreamDestroy(h->run);
+    if (h->evx) cudaEventDestroy(h->evx);
     if (h->ev0) cudaEventDestroy(h->ev0);
     if (h->ev1) cudaEventDestroy(h->ev1);
     for (cudaEvent_t e : h->evpool) cudaEventDestroy(e);
@@ -914,6 +967,63 @@ mg_status pressure_solve(mg_handle* h, const double* b, double* x, double tol, m
     auto A = [&](const double* z, double* w, int j, cudaStream_t q) { return apply_gcr(h, z, w, j, q); };
     auto P = [&](const double* r, double* z, cudaStream_t q) { return run_vcycle(h, r, z, q); };
     return gcr(h, 0, cells(h, 0), b, x, tol, info, s, A, P);
+}
+
+mg_status ensemble_pressure_solve(mg_handle* const* handles, int32_t count, const double* const* b,
+                                  double* const* x, double tol, mg_solve_info* infos, int32_t* statuses,
+                                  void* stream) {
+    if (count < 0 || (count > 0 && (!handles || !b || !x)) || !(tol >= 0.0)) return MG_ERR_ARG;
+    if (count == 0) return MG_OK;
+    for (int i = 0; i < count; ++i) {
+        if (!handles[i] || !b[i] || !x[i] || b[i] == x[i] || handles[i]->device != handles[0]->device)
+            return MG_ERR_ARG;
+        for (int k = 0; k < i; ++k)
+            if (handles[k] == handles[i]) return MG_ERR_ARG;   // a handle holds one solve's workspace
+    }
+    DeviceGuard dg(handles[0]->device);
+    // every member starts after the work already queued on the caller's stream
+    CK(cudaEventRecord(handles[0]->evx, S(stream)));
+    std::vector<GcrRun> g(count);
+    for (int i = 0; i < count; ++i) {
+        mg_handle* h = handles[i];
+        g[i].sys = 0;
+        g[i].n = cells(h, 0);
+        g[i].x = x[i];
+        g[i].tol = tol;
+        CK(cudaStreamWaitEvent(h->run, handles[0]->evx, 0));
+        TRY(gcr_start(h, g[i], b[i], h->run));
+    }
+    for (int i = 0; i < count; ++i) {
+        CK(cudaStreamSynchronize(handles[i]->run));
+        gcr_started(handles[i], g[i]);
+    }
+    // rounds: every unfinished member launches one iteration on its stream (the members run
+    // side by side on the GPU), then the host collects the residual norms
+    for (bool any = true; any;) {
+        any = false;
+        for (int i = 0; i < count; ++i) {
+            if (!g[i].active) continue;
+            mg_handle* h = handles[i];
+            auto A = [h](const double* z, double* w, int j, cudaStream_t q) { return apply_gcr(h, z, w, j, q); };
+            auto P = [h](const double* r, double* z, cudaStream_t q) { return run_vcycle(h, r, z, q); };
+            TRY(gcr_launch(h, g[i], h->run, A, P));
+        }
+        for (int i = 0; i < count; ++i) {
+            if (!g[i].active) continue;
+            CK(cudaStreamSynchronize(handles[i]->run));
+            TRY(gcr_landed(handles[i], g[i], handles[i]->run));
+            any = any || g[i].active;
+        }
+    }
+    mg_status st = MG_OK;
+    for (int i = 0; i < count; ++i) CK(cudaEventRecord(handles[i]->ev1, handles[i]->run));
+    for (int i = 0; i < count; ++i) {
+        CK(cudaEventSynchronize(handles[i]->ev1));
+        gcr_info(handles[i], g[i], infos ? infos + i : nullptr);
+        if (statuses) statuses[i] = g[i].st;
+        if (st == MG_OK) st = g[i].st;
+    }
+    return st;
 }
 
 mg_status mixed_solve(mg_handle* h, const double* rhs_u, const double* rhs_p, double* u, double* p, double tol,

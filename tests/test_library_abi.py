@@ -91,4 +91,8 @@ def test_null_handle_calls_are_rejected(lib):
     assert lib.pressure_solve(None, vp(8), vp(16), 1e-8, None, None) == -1
     assert lib.mixed_solve(None, vp(8), vp(16), vp(24), vp(32), 1e-8, None, None) == -1
     assert lib.mg_sizes(None, None, None, None) == -1
+    assert lib.ensemble_pressure_solve(None, 0, None, None, 1e-8, None, None, None) == 0    # nothing to do
+    assert lib.ensemble_pressure_solve(None, 1, None, None, 1e-8, None, None, None) == -1
+    hs = (ctypes.c_void_p * 1)(None)
+    assert lib.ensemble_pressure_solve(hs, 1, hs, hs, 1e-8, None, None, None) == -1     # NULL member
     lib.mg_destroy(None)
