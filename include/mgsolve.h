@@ -178,6 +178,16 @@ mg_status mg_residual_restrict(mg_handle* h, int32_t level, const double* b, con
 /* x += Prolongate(xc) from level+1 onto level (Eq. prolongation, natural injection). */
 mg_status mg_prolong_add(mg_handle* h, int32_t level, const double* xc, double* x, void* stream);
 
+/* Adjoint of pressure_solve: lambda = H^-T g, the gradient dL/db of a loss L(x) of the solution
+ * x = H^-1 b given g = dL/dx (the differentiable solve of the batched-ensemble and data
+ * assimilation uses).  The strong-form H of this library has V H symmetric (V the cell
+ * volumes, Sec. 3.5: the flux through a face is the same seen from both cells), so
+ * H^T = V H V^-1 and lambda = V H^-1 (V^-1 g): the same GCR and V-cycle as pressure_solve on
+ * the right-hand side V^-1 g, then a multiplication by V.  tol applies to that solve.
+ *   g, lambda  DEVICE, N doubles each, g != lambda.  Synchronous. */
+mg_status pressure_solve_adjoint(mg_handle* h, const double* g, double* lambda, double tol,
+                                 mg_solve_info* info, void* stream);
+
 /* Ensemble of independent pressure solves (the batched-ensemble use of Sec. 4.1's solver:
  * many members, each its own mesh, levels and precision): handles[i] solves
  * H_i x[i] = b[i] exactly as pressure_solve does (same kernels in the same order, so the

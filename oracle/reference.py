@@ -84,6 +84,12 @@ def direct_solve(A: sp.spmatrix, b: np.ndarray) -> np.ndarray:
     return spla.spsolve(A.tocsc(), b)
 
 
+def adjoint_solve(A: sp.spmatrix, g: np.ndarray) -> np.ndarray:
+    """lambda = A^{-T} g: the gradient dL/db of L(x(b)), x = A^{-1} b, given g = dL/dx (the
+    plain definition, a direct solve with the transposed matrix)."""
+    return direct_solve(sp.csr_matrix(A.T), g)
+
+
 def iterative_reference(A: sp.spmatrix, b: np.ndarray, P, tol: float = 1e-12,
                         maxiter: int = 400) -> np.ndarray:
     """GCR on the assembled matrix to a relative residual ``tol`` (checked again at the end)."""

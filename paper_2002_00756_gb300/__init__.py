@@ -71,6 +71,7 @@ _SIGS = {
     "helmholtz_apply": [_VP, _DP, _DP, _VP],
     "vcycle": [_VP, _DP, _DP, _VP],
     "pressure_solve": [_VP, _DP, _DP, _D, ctypes.POINTER(_Info), _VP],
+    "pressure_solve_adjoint": [_VP, _DP, _DP, _D, ctypes.POINTER(_Info), _VP],
     "ensemble_pressure_solve": [_VP, _I32, _VP, _VP, _D, ctypes.POINTER(_Info), ctypes.POINTER(ctypes.c_int32),
                                 _VP],
     "mixed_solve": [_VP, _DP, _DP, _DP, _DP, _D, ctypes.POINTER(_Info), _VP],
@@ -250,6 +251,52 @@ def pressure_solve(h: Handle, b, x, tol: float = 1e-8, stream=None) -> SolveInfo
     st = load().pressure_solve(h.ptr, _ptr(b, h.ncell, "b"), _ptr(x, h.ncell, "x"), tol, ctypes.byref(info),
                                _stream(stream))
     return _solve_status(st, info, "pressure_solve")
+
+
+def pressure_solve_adjoint(h: Handle, g, lam, tol: float = 1e-8, stream=None) -> SolveInfo:
+    """lam = H^-T g (see pressure_solve_adjoint in mgsolve.h)."""
+    info = _Info()
+    st = load().pressure_solve_adjoint(h.ptr, _ptr(g, h.ncell, "g"), _ptr(lam, h.ncell, "lambda"), tol,
+                                       ctypes.byref(info), _stream(stream))
+    return _solve_status(st, info, "pressure_solve_adjoint")
+
+
+def _pressure_solve_function():
+    import torch
+
+    class PressureSolve(torch.autograd.Function):
+        """x = H^-1 b with dL/db = H^-T dL/dx (both solves in the library)."""
+
+        @staticmethod
+        def forward(ctx, b, h, tol):
+            x = torch.zeros_like(b)
+            info = pressure_solve(h, b.contiguous(), x, tol=tol)
+            if not info.converged:
+                raise MGError(info.status, "pressure_solve")
+            ctx.h, ctx.tol = h, tol
+            return x
+
+        @staticmethod
+        def backward(ctx, gx):
+            lam = torch.zeros_like(gx)
+            info = pressure_solve_adjoint(ctx.h, gx.contiguous(), lam, tol=ctx.tol)
+            if not info.converged:
+                raise MGError(info.status, "pressure_solve_adjoint")
+            return lam, None, None
+
+    return PressureSolve
+
+
+def solve(h: Handle, b, tol: float = 1e-8):
+    """Differentiable pressure solve: x = H^-1 b as a torch operation (float64 CUDA tensor b);
+    its backward pass is the adjoint solve."""
+    global _PS
+    if _PS is None:
+        _PS = _pressure_solve_function()
+    return _PS.apply(b, h, tol)
+
+
+_PS = None
 
 
 def ensemble_pressure_solve(handles, bs, xs, tol: float = 1e-8, stream=None) -> list[SolveInfo]:

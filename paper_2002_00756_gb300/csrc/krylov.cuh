@@ -91,6 +91,16 @@ __device__ bool grid_reduce(double (&v)[ND], double* partials, unsigned int* tic
     return threadIdx.x == 0;
 }
 
+// out = V x (multiply) or V^-1 x, V = area[col] * dz[k] the finest level's cell volumes
+__global__ void k_scale_volume(int ncol, int nlev, const double* __restrict__ area, const double* __restrict__ dz,
+                               const double* x, double* out, bool multiply) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x, k = blockIdx.y;
+    if (c >= ncol || k >= nlev) return;
+    const size_t e = (size_t)k * ncol + c;
+    const double v = __ldg(area + c) * __ldg(dz + k);
+    out[e] = multiply ? x[e] * v : x[e] / v;
+}
+
 // out = <a, b>
 __global__ void __launch_bounds__(RED_THREADS) k_dot(size_t n, const double* __restrict__ a,
                                                      const double* __restrict__ b, double* partials,
@@ -122,17 +132,6 @@ __device__ void gcr_coeffs(const double (&t)[J + 2], GcrScal* S) {
     S->alpha[J] = t[J + 1] / ww;
 }
 
-// FP64 -> FP32 by truncation of the significand, in integer operations (GB300's FP64 pipe
-// issues 2 lanes per clock per SM, the integer units far more).  Values below the FP32
-// normal range give 0; FP32 overflow, infinities and NaN take the hardware conversion.
-__device__ __forceinline__ float narrow_f32(double v) {
-    const unsigned hi = (unsigned)__double2hiint(v), lo = (unsigned)__double2loint(v);
-    const unsigned mag = hi & 0x7fffffffu;
-    if (mag < 0x38100000u) return 0.f;
-    if (mag >= 0x47f00000u) return (float)v;
-    // rebias the exponent (1023 -> 127: subtract 896 << 20) and keep 23 significand bits
-    return __uint_as_float(__funnelshift_l(lo, mag - 0x38000000u, 3) | (hi & 0x80000000u));
-}
 
 template <int J>
 __device__ __forceinline__ void gcr_accumulate(double (&v)[J + 2], double we, double re,
@@ -157,9 +156,9 @@ __global__ void __launch_bounds__(RED_THREADS) k_gcr_sums(size_t n, const double
     if (grid_reduce<J + 2>(v, partials, ticket, t)) gcr_coeffs<J>(t, S);
 }
 
-// w_J <- w_J - sum_i beta_i w_i (stored in place), r <- r - alpha_J w_J, then <r, r> -> rr.
-// <r, r> only decides convergence: each thread sums its share in FP32 (relative error about
-// 1e-6 of rr, 5e-7 of the reported relative residual), the grid sum is FP64.
+// w_J <- w_J - sum_i beta_i w_i (stored in place), r <- r - alpha_J w_J, then <r, r> -> rr
+// (FP64: the residual spans the right-hand side's whole range, whose squares FP32 would
+// flush to zero below about 1e-19).
 template <int J>
 __global__ void __launch_bounds__(RED_THREADS) k_gcr_orth_update(size_t n, double* __restrict__ Wb, size_t ld,
                                                                  double* __restrict__ r, double* partials,
@@ -169,7 +168,7 @@ __global__ void __launch_bounds__(RED_THREADS) k_gcr_orth_update(size_t n, doubl
     for (int i = 0; i < J; ++i) beta[i] = S->beta[J * MAXR + i];
     const double a = S->alpha[J];
     double* w = Wb + (size_t)J * ld;
-    float rrf = 0.f;
+    double v[1] = {0.0}, t[1];
     for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
         double we = w[e];
 #pragma unroll
@@ -177,10 +176,8 @@ __global__ void __launch_bounds__(RED_THREADS) k_gcr_orth_update(size_t n, doubl
         if (J > 0) w[e] = we;
         const double re = r[e] - a * we;
         r[e] = re;
-        const float rf = narrow_f32(re);
-        rrf = fmaf(rf, rf, rrf);
+        v[0] += re * re;
     }
-    double v[1] = {(double)rrf}, t[1];
     if (grid_reduce<1>(v, partials, ticket, t)) S->rr = t[0];
 }
 

@@ -81,6 +81,9 @@ struct mg_handle {
     double* rdz64 = nullptr;
     float* rdz32 = nullptr;
     double* a6 = nullptr;       // finest level: six premultiplied FP64 couplings and 1 + their sum, per cell
+    double* area0 = nullptr;    // finest level: column areas and layer depths (cell volumes, adjoint solve)
+    double* dz = nullptr;
+    double* adj = nullptr;      // [N] the scaled right-hand side of the adjoint solve
     // GCR
     size_t glen = 0;            // length of a GCR vector (N, or nu + N with mixed data)
     double* Z = nullptr;        // [restart][glen]
@@ -737,6 +740,8 @@ mg_status setup_impl(mg_handle* h, const mg_mesh* mesh, const mg_params* prm, co
     std::vector<double> rdz(nlev);
     for (int k = 0; k < nlev; ++k) rdz[k] = 1.0 / vg.dz[k];
     TRY(upload(h, &h->rdz64, rdz));
+    TRY(upload(h, &h->dz, vg.dz));
+    TRY(upload(h, &h->area0, hg[0].area));
     TRY(upload(h, &h->rdz32, rdz));
     const int prec = prm->vcycle_precision;
     h->lv.resize(L);
@@ -849,6 +854,7 @@ mg_status setup_impl(mg_handle* h, const mg_mesh* mesh, const mg_params* prm, co
     TRY(dalloc(h, &h->Z, (size_t)prm->gcr_restart * h->glen));
     TRY(dalloc(h, &h->W, (size_t)prm->gcr_restart * h->glen));
     TRY(dalloc(h, &h->r, h->glen));
+    TRY(dalloc(h, &h->adj, N0));
     TRY(dalloc(h, &h->gs, 1));
     {
         const size_t apply_blocks = (size_t)((ncol0 + mg::RED_THREADS - 1) / mg::RED_THREADS) *
@@ -967,6 +973,32 @@ mg_status pressure_solve(mg_handle* h, const double* b, double* x, double tol, m
     auto A = [&](const double* z, double* w, int j, cudaStream_t q) { return apply_gcr(h, z, w, j, q); };
     auto P = [&](const double* r, double* z, cudaStream_t q) { return run_vcycle(h, r, z, q); };
     return gcr(h, 0, cells(h, 0), b, x, tol, info, s, A, P);
+}
+
+mg_status pressure_solve_adjoint(mg_handle* h, const double* g, double* lambda, double tol, mg_solve_info* info,
+                                 void* stream) {
+    if (!h || !g || !lambda || g == lambda || !(tol >= 0.0)) return MG_ERR_ARG;
+    DeviceGuard dg(h->device);
+    cudaStream_t s = S(stream);
+    const int ncol = h->lv[0].ncol, nlev = h->nlev;
+    const size_t n = cells(h, 0);
+    const dim3 grid((ncol + 127) / 128, nlev);
+    // H^T = V H V^-1 (V H is symmetric): lambda = V H^-1 (V^-1 g)
+    {
+        Prof pr(h, MG_K_DOT, 0, 16.0 * n, s);
+        mg::k_scale_volume<<<grid, 128, 0, s>>>(ncol, nlev, h->area0, h->dz, g, h->adj, false);
+        CK(cudaGetLastError());
+    }
+    auto A = [&](const double* z, double* w, int j, cudaStream_t q) { return apply_gcr(h, z, w, j, q); };
+    auto P = [&](const double* r, double* z, cudaStream_t q) { return run_vcycle(h, r, z, q); };
+    const mg_status st = gcr(h, 0, n, h->adj, lambda, tol, info, s, A, P);
+    if (st == MG_OK || st == MG_ERR_NOT_CONVERGED) {
+        Prof pr(h, MG_K_DOT, 0, 16.0 * n, s);
+        mg::k_scale_volume<<<grid, 128, 0, s>>>(ncol, nlev, h->area0, h->dz, lambda, lambda, true);
+        CK(cudaGetLastError());
+        CK(cudaStreamSynchronize(s));
+    }
+    return st;
 }
 
 mg_status ensemble_pressure_solve(mg_handle* const* handles, int32_t count, const double* const* b,

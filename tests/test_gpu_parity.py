@@ -343,3 +343,18 @@ def test_mixed_solve(mg, name, precision):
     perr = np.linalg.norm(got[S.nu:] - xs[S.nu:]) / np.linalg.norm(xs[S.nu:])
     print(f"{name} {precision}: iters {info.iters}, error {err:.2e}, pressure error {perr:.2e}")
     assert err <= 1e-8 and perr <= 1e-8
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_solve_is_scale_invariant(mg, precision):
+    """H x = 2^-70 b gives 2^-70 x, bit for bit, in the same iterations: every scalar of GCR and
+    every value of the V-cycle scales by a power of two (residual norms down to 1e-30 and
+    their squares included), so no step may flush, saturate or stop early on small data."""
+    cfg, inp, hier = problem("c12")
+    h = mg.mg_setup_config(cfg, inp, precision=precision)
+    b = dev(inp["rhs"])
+    x1, x2 = torch.zeros_like(b), torch.zeros_like(b)
+    i1 = mg.pressure_solve(h, b, x1, tol=1e-10)
+    i2 = mg.pressure_solve(h, b * 2.0 ** -70, x2, tol=1e-10)
+    assert i1.converged and i2.converged and i1.iters == i2.iters, (i1, i2)
+    assert torch.equal(x2, x1 * 2.0 ** -70)

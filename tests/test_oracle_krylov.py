@@ -70,3 +70,25 @@ def test_mg_preconditioned_gcr_matches_direct_solve():
 def test_breakdown_is_reported():
     with pytest.raises(FloatingPointError):
         gcr(lambda v: 0 * v, np.ones(4), None, tol=1e-8)
+
+
+def test_adjoint_solve_satisfies_the_adjoint_identity_and_the_volume_similarity():
+    """adjoint_solve: <A^-T g, b> = <g, A^-1 b> for every b, g; and for the Helmholtz
+    operator A^T = V A V^-1 with V the cell volumes (area x layer depth, closed forms of the
+    geometry), the relation the GPU adjoint solve relies on."""
+    from oracle.problem import pressure_hierarchy
+    from oracle.reference import adjoint_solve
+    cfg = syn.small_config(4, 5, levels=1, seed=syn.BASE_SEED + 41)
+    inp = syn.make_inputs(cfg)
+    H = pressure_hierarchy(cfg, inp).levels[0]
+    A = assemble_helmholtz(H)
+    rng = np.random.default_rng(3)
+    g, b = rng.standard_normal(cfg.ncell), rng.standard_normal(cfg.ncell)
+    lam, x = adjoint_solve(A, g), direct_solve(A, b)
+    assert abs(lam @ b - g @ x) <= 1e-12 * np.linalg.norm(lam) * np.linalg.norm(b)
+    V = (H.mesh.area[None, :] * H.mesh.dz[:, None]).ravel()
+    D = A.toarray()
+    assert np.allclose(D.T, V[:, None] * D / V[None, :], rtol=1e-12, atol=1e-12 * np.abs(D).max())
+    # and a plain mistake (the untransposed solve) is caught by the identity
+    x2 = direct_solve(A, g)
+    assert abs(x2 @ b - g @ x) > 1e-6 * np.linalg.norm(x2) * np.linalg.norm(b)
