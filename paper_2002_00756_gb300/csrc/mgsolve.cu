@@ -29,6 +29,12 @@
 #ifndef MG_RESTRICT_KCHUNK
 #define MG_RESTRICT_KCHUNK 8
 #endif
+#ifndef MG_RESTRICT_KCHUNK_BIG
+#define MG_RESTRICT_KCHUNK_BIG 24
+#endif
+#ifndef MG_RESTRICT_BIG_NCOL
+#define MG_RESTRICT_BIG_NCOL 100000
+#endif
 #ifndef MG_RESTRICT_SHAL
 #define MG_RESTRICT_SHAL 2
 #endif
@@ -316,7 +322,9 @@ mg_status launch_restrict(mg_handle* h, int lev, const Lvl<T, C>& L, const X* x,
     if (L.n % 16 == 0) {
         // one thread per fine column, 4 warps per block
         const int warps = 6 * (L.n / 2) * (L.n / 16);
-        const int kc = MG_RESTRICT_KCHUNK;
+        // levels per thread: on a level large enough to fill the GPU several times over, long
+        // chunks (fewer prologues); smaller levels need the threads of short chunks
+        const int kc = L.ncol >= MG_RESTRICT_BIG_NCOL ? MG_RESTRICT_KCHUNK_BIG : MG_RESTRICT_KCHUNK;
         const dim3 grid((warps + 3) / 4, (L.nlev + kc - 1) / kc);
         mg::k_resid_restrict16<T, C, XZERO, X, B, O, MG_RESTRICT_SHAL><<<grid, 128, 0, s>>>(L, x, b, w, bc, ncol_c,
                                                                                            kc);
