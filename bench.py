@@ -225,6 +225,46 @@ def run_reference(args, cfg, inp, world, rank):
     print(json.dumps(line), flush=True)
 
 
+def run_adjoint(args, cfg, inp, mg, torch, world, rank):
+    """The differentiable solve: forward x = H^-1 b and backward dL/db = H^-T dL/dx through the
+    torch autograd wrapper, L = <w, x> (C96L70 by default)."""
+    h = mg.mg_setup_config(cfg, inp, precision=args.precision, mixed=False)
+    b0 = torch.from_numpy(inp["rhs"]).cuda()
+    wv = torch.from_numpy(syn.normal(cfg.seed, 99, cfg.ncell)).cuda()
+
+    def step():
+        b = b0.clone().requires_grad_(True)
+        x = mg.solve(h, b, tol=args.tol)
+        (wv * x).sum().backward()
+        return b.grad
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with Clocks(0) as clk:
+        e0.record()
+        for _ in range(args.steps):
+            step()
+        e1.record()
+        torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    xf = torch.zeros_like(b0)
+    fwd = mg.pressure_solve(h, b0, xf, tol=args.tol)
+    adj = mg.pressure_solve_adjoint(h, wv, torch.zeros_like(b0), tol=args.tol)
+    line = {
+        "metric": f"ms per forward + backward pressure solve (autograd) at C{cfg.n}L{cfg.nlev}",
+        "value": round(ms, 4), "unit": "ms", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "higher_is_better": False, "dtype": "f64" if args.precision == "fp64" else "f64+f32", "data": "synthetic",
+        "config": {"workload": f"{workload_name(cfg, args.precision)}; loss <w, x>, dL/db by the adjoint solve",
+                   "forward_iters": fwd.iters, "adjoint_iters": adj.iters},
+        "clocks": clk.result,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    h.destroy()
+
+
 ENSEMBLE = [(n, nlev) for n in (32, 40, 48, 64, 80, 96, 112, 128) for nlev in (30, 50, 70)]
 
 
@@ -354,7 +394,7 @@ def main():
                     help="time step in s (default: the workload's, 600 s; 1200 s gives CFL_h ~ 7.9 at C192, "
                          "the paper's regime for the robustness sweep)")
     ap.add_argument("--levels", type=int, default=None, help="multigrid levels (default: the workload's)")
-    ap.add_argument("--system", default="pressure", choices=["pressure", "mixed", "ensemble"],
+    ap.add_argument("--system", default="pressure", choices=["pressure", "mixed", "ensemble", "adjoint"],
                     help="mixed: the (u, p) solve (GCR + Schur-complement multigrid) on the C48L30 "
                          "mixed workload instead of the headline pressure solve")
     ap.add_argument("--tol", type=float, default=1e-8)
@@ -368,7 +408,9 @@ def main():
     world, rank, local = dist_init()
     if args.system == "mixed" and args.workload == "c192":
         args.workload = "c48"
-    if args.impl == "reference" and args.system == "ensemble":
+    if args.system == "adjoint" and args.workload == "c192":
+        args.workload = "c96"
+    if args.impl == "reference" and args.system in ("ensemble", "adjoint"):
         if rank == 0:
             print(json.dumps({"impl": "reference", "unavailable": "the reference arm times the pressure solve "
                                                                   "only (the headline metric)"}))
@@ -404,6 +446,8 @@ def main():
         return run_mixed(args, cfg, inp, mg, torch, world, rank)
     if args.system == "ensemble":
         return run_ensemble(args, mg, torch, world, rank)
+    if args.system == "adjoint":
+        return run_adjoint(args, cfg, inp, mg, torch, world, rank)
 
     if args.profile_solve:
         h = mg.mg_setup_config(cfg, inp, precision=args.precision, mixed=False, max_iter=args.iters)
