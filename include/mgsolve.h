@@ -188,6 +188,15 @@ mg_status mg_prolong_add(mg_handle* h, int32_t level, const double* xc, double* 
 mg_status pressure_solve_adjoint(mg_handle* h, const double* g, double* lambda, double tol,
                                  mg_solve_info* info, void* stream);
 
+/* Gradient of a loss L(x), x = H^-1 b, with respect to the six couplings a_{i,f} of every
+ * finest-level cell (the strong-form coefficients of Eq. helmholtz_operator): from
+ * H x = b, dL = -<lambda, dH x> with lambda = H^-T dL/dx (pressure_solve_adjoint), so
+ *     grad[s * N + i] = dL/da_{i,s} = -lambda_i (x_i - x_{j(i,s)}),
+ * s = 0..5 for the E, W, N, S, upper and lower neighbour (0 where there is none: top and
+ * bottom of a column).  lambda, x: DEVICE, N doubles; grad: DEVICE, 6 N doubles. */
+mg_status helmholtz_coefficient_gradient(mg_handle* h, const double* lambda, const double* x, double* grad,
+                                         void* stream);
+
 /* Ensemble of independent pressure solves (the batched-ensemble use of Sec. 4.1's solver:
  * many members, each its own mesh, levels and precision): handles[i] solves
  * H_i x[i] = b[i] exactly as pressure_solve does (same kernels in the same order, so the

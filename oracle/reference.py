@@ -90,6 +90,21 @@ def adjoint_solve(A: sp.spmatrix, g: np.ndarray) -> np.ndarray:
     return direct_solve(sp.csr_matrix(A.T), g)
 
 
+def coefficient_gradient(H: Level, x: np.ndarray, lam: np.ndarray) -> np.ndarray:
+    """dL/da for L(x), x = H^{-1} b, given lam = H^{-T} dL/dx: differentiating H x = b gives
+    dL = -<lam, dH x>, and (dH x)_i = sum_f da_{i,f} (x_i - x_j), so
+        dL/da_{i,f} = -lam_i (x_i - x_{j(f)}).
+    Returned as (6, nlev, ncol): E, W, N, S, up, down (zero where a face has no neighbour)."""
+    x = np.asarray(x, dtype=np.float64).reshape(H.shape)
+    lam = np.asarray(lam, dtype=np.float64).reshape(H.shape)
+    out = np.zeros((6,) + H.shape)
+    for d in range(4):
+        out[d] = -lam * (x - x[:, H.mesh.nbr[d]])
+    out[4, :-1] = -lam[:-1] * (x[:-1] - x[1:])
+    out[5, 1:] = -lam[1:] * (x[1:] - x[:-1])
+    return out
+
+
 def iterative_reference(A: sp.spmatrix, b: np.ndarray, P, tol: float = 1e-12,
                         maxiter: int = 400) -> np.ndarray:
     """GCR on the assembled matrix to a relative residual ``tol`` (checked again at the end)."""

@@ -72,6 +72,7 @@ _SIGS = {
     "vcycle": [_VP, _DP, _DP, _VP],
     "pressure_solve": [_VP, _DP, _DP, _D, ctypes.POINTER(_Info), _VP],
     "pressure_solve_adjoint": [_VP, _DP, _DP, _D, ctypes.POINTER(_Info), _VP],
+    "helmholtz_coefficient_gradient": [_VP, _DP, _DP, _DP, _VP],
     "ensemble_pressure_solve": [_VP, _I32, _VP, _VP, _D, ctypes.POINTER(_Info), ctypes.POINTER(ctypes.c_int32),
                                 _VP],
     "mixed_solve": [_VP, _DP, _DP, _DP, _DP, _D, ctypes.POINTER(_Info), _VP],
@@ -259,6 +260,13 @@ def pressure_solve_adjoint(h: Handle, g, lam, tol: float = 1e-8, stream=None) ->
     st = load().pressure_solve_adjoint(h.ptr, _ptr(g, h.ncell, "g"), _ptr(lam, h.ncell, "lambda"), tol,
                                        ctypes.byref(info), _stream(stream))
     return _solve_status(st, info, "pressure_solve_adjoint")
+
+
+def helmholtz_coefficient_gradient(h: Handle, lam, x, grad, stream=None):
+    """grad (6 N, E/W/N/S/up/down blocks) = dL/da = -lam_i (x_i - x_j), see mgsolve.h."""
+    _check(load().helmholtz_coefficient_gradient(h.ptr, _ptr(lam, h.ncell, "lambda"), _ptr(x, h.ncell, "x"),
+                                                 _ptr(grad, 6 * h.ncell, "grad"), _stream(stream)),
+           "helmholtz_coefficient_gradient")
 
 
 def _pressure_solve_function():

@@ -101,6 +101,20 @@ __global__ void k_scale_volume(int ncol, int nlev, const double* __restrict__ ar
     out[e] = multiply ? x[e] * v : x[e] / v;
 }
 
+// grad[s][e] = -lam_e (x_e - x_(neighbour s of e)), s = E, W, N, S, up, down (0 without a
+// neighbour): the gradient of L(x) with respect to the six couplings of the finest level
+__global__ void k_coef_grad(Lvl<double, double> L, const double* __restrict__ lam, const double* __restrict__ x,
+                            double* __restrict__ grad) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x, k = blockIdx.y;
+    if (c >= L.ncol || k >= L.nlev) return;
+    const size_t ncol = L.ncol, N = (size_t)L.nlev * ncol, e = (size_t)k * ncol + c;
+    const double l = lam[e], x0 = x[e];
+#pragma unroll
+    for (int s = 0; s < 4; ++s) grad[s * N + e] = -l * (x0 - x[(size_t)k * ncol + __ldg(L.nbr + s * ncol + c)]);
+    grad[4 * N + e] = k + 1 < L.nlev ? -l * (x0 - x[e + ncol]) : 0.0;
+    grad[5 * N + e] = k > 0 ? -l * (x0 - x[e - ncol]) : 0.0;
+}
+
 // out = <a, b>
 __global__ void __launch_bounds__(RED_THREADS) k_dot(size_t n, const double* __restrict__ a,
                                                      const double* __restrict__ b, double* partials,

@@ -1009,6 +1009,18 @@ mg_status pressure_solve_adjoint(mg_handle* h, const double* g, double* lambda, 
     return st;
 }
 
+mg_status helmholtz_coefficient_gradient(mg_handle* h, const double* lambda, const double* x, double* grad,
+                                         void* stream) {
+    if (!h || !lambda || !x || !grad) return MG_ERR_ARG;
+    DeviceGuard dg(h->device);
+    cudaStream_t s = S(stream);
+    const Lvl<double, double> L = View<double, double>::lvl(h, 0);
+    Prof pr(h, MG_K_DOT, 0, 64.0 * cells(h, 0), s);   // lambda, x (read), 6 gradients (written)
+    mg::k_coef_grad<<<dim3((L.ncol + 127) / 128, L.nlev), 128, 0, s>>>(L, lambda, x, grad);
+    CK(cudaGetLastError());
+    return MG_OK;
+}
+
 mg_status ensemble_pressure_solve(mg_handle* const* handles, int32_t count, const double* const* b,
                                   double* const* x, double tol, mg_solve_info* infos, int32_t* statuses,
                                   void* stream) {

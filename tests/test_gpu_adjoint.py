@@ -68,3 +68,22 @@ def test_autograd_gradient(setup, precision):
             an = float((grad * d).sum())
             assert abs(fd - an) <= 1e-8 * (abs(an) + float(w.norm() * d.norm()) * 1e-3)
     h.destroy()
+
+
+def test_coefficient_gradient(setup):
+    """helmholtz_coefficient_gradient against the oracle's dL/da = -lam_i (x_i - x_j) (itself
+    pinned by central differences), evaluated at the oracle's own x and lambda."""
+    from oracle.problem import pressure_hierarchy
+    from oracle.reference import adjoint_solve, coefficient_gradient, direct_solve
+    mg, cfg, inp, A = setup
+    H = pressure_hierarchy(cfg, inp).levels[0]
+    x = direct_solve(A, inp["rhs"])
+    lam = adjoint_solve(A, syn.normal(48, 0, cfg.ncell))
+    ref = coefficient_gradient(H, x, lam).reshape(6, -1)
+    h = mg.mg_setup_config(cfg, inp)
+    grad = torch.full((6 * cfg.ncell,), float("nan"), dtype=torch.float64, device="cuda")
+    mg.helmholtz_coefficient_gradient(h, torch.from_numpy(lam).cuda(), torch.from_numpy(x).cuda(), grad)
+    got = grad.cpu().numpy().reshape(6, -1)
+    # one product of a difference per entry: rounding of the last bits only
+    assert np.allclose(got, ref, rtol=1e-14, atol=1e-14 * np.abs(ref).max())
+    h.destroy()

@@ -92,3 +92,33 @@ def test_adjoint_solve_satisfies_the_adjoint_identity_and_the_volume_similarity(
     # and a plain mistake (the untransposed solve) is caught by the identity
     x2 = direct_solve(A, g)
     assert abs(x2 @ b - g @ x) > 1e-6 * np.linalg.norm(x2) * np.linalg.norm(b)
+
+
+def test_coefficient_gradient_matches_central_differences():
+    """dL/da_{i,f} = -lam_i (x_i - x_j) (oracle.reference.coefficient_gradient) against central
+    differences of L = <w, H(a)^-1 b> in single coefficients, horizontal and vertical."""
+    from oracle.problem import pressure_hierarchy
+    from oracle.reference import adjoint_solve, coefficient_gradient
+    cfg = syn.small_config(4, 5, levels=1, seed=syn.BASE_SEED + 51)
+    inp = syn.make_inputs(cfg)
+    H = pressure_hierarchy(cfg, inp).levels[0]
+    b = inp["rhs"]
+    w = syn.normal(52, 0, cfg.ncell)
+    A = assemble_helmholtz(H)
+    x = direct_solve(A, b)
+    G = coefficient_gradient(H, x, adjoint_solve(A, w))
+
+    def loss():
+        return w @ direct_solve(assemble_helmholtz(H), b)
+
+    for (arr, idx, gi) in [(H.a_h[0], (2, 5), (0, 2, 5)), (H.a_h[3], (1, 17), (3, 1, 17)),
+                           (H.a_up, (1, 9), (4, 1, 9)), (H.a_dn, (3, 30), (5, 3, 30))]:
+        a0 = arr[idx]
+        h = 1e-4 * a0
+        arr[idx] = a0 + h
+        lp = loss()
+        arr[idx] = a0 - h
+        lm = loss()
+        arr[idx] = a0
+        fd = (lp - lm) / (2 * h)
+        assert abs(fd - G[gi]) <= 1e-6 * abs(G[gi]) + 1e-12, (gi, fd, G[gi])
