@@ -24,6 +24,11 @@ CASES = {
     "c5l3": (syn.small_config(5, 3, levels=1, seed=syn.BASE_SEED + 12), None),
     "c4l1": (syn.small_config(4, 1, levels=3, seed=syn.BASE_SEED + 13), None),
     "c20l9": (syn.small_config(20, 9, levels=3, seed=syn.BASE_SEED + 14), None),
+    # degenerate meshes: one cell per panel (every neighbour on another panel), and a
+    # hierarchy whose coarsest level is that mesh, with a single-level column
+    "c1l4": (syn.small_config(1, 4, levels=1, seed=syn.BASE_SEED + 61), None),
+    "c2l3": (syn.small_config(2, 3, levels=2, seed=syn.BASE_SEED + 62), None),
+    "c2l1": (syn.small_config(2, 1, levels=2, seed=syn.BASE_SEED + 63), None),
 }
 
 
@@ -94,7 +99,7 @@ def test_level_apply_every_level(mg, name):
         assert np.all(np.abs(host(y) - H.apply(x).ravel()) <= 1e-12 * abs_apply_scale(H, x)), l
 
 
-@pytest.mark.parametrize("name", ["c12", "c6l7", "c4l1", "c20l9"])
+@pytest.mark.parametrize("name", ["c12", "c6l7", "c4l1", "c20l9", "c2l3", "c1l4"])
 @pytest.mark.parametrize("sweeps,start", [(1, "zero"), (2, "zero"), (1, "random"), (3, "random")])
 def test_block_jacobi_sweeps(mg, name, sweeps, start):
     cfg, inp, hier = problem(name)
@@ -162,7 +167,7 @@ def test_vcycle_smoothing_counts(mg, n_pre, n_post, n_coarse):
 
 
 @pytest.mark.parametrize("precision,tol", [("fp32", 1e-4), ("fp32_bf16", 5e-2)])
-@pytest.mark.parametrize("name", ["c12", "c20l9", "c5l3"])
+@pytest.mark.parametrize("name", ["c12", "c20l9", "c5l3", "c2l3"])
 def test_vcycle_reduced_precision(mg, name, precision, tol):
     cfg, inp, hier = problem(name)
     h = mg.mg_setup_config(cfg, inp, precision=precision)
@@ -209,7 +214,7 @@ def _xstar(name):
 
 
 @pytest.mark.parametrize("precision", ["fp64", "fp32", "fp32_bf16"])
-@pytest.mark.parametrize("name", ["c12", "c20l9", "c5l3"])
+@pytest.mark.parametrize("name", ["c12", "c20l9", "c5l3", "c2l3", "c1l4"])
 def test_pressure_solve(mg, name, precision):
     from oracle.krylov import gcr
     cfg, inp, hier = problem(name)
