@@ -291,6 +291,7 @@ def test_graph_replay_matches_direct_launches(mg):
 
 MIXED = {
     "m4l6": syn.small_config(4, 6, levels=2, seed=syn.BASE_SEED + 21, mixed=True),
+    "m2l4": syn.small_config(2, 4, levels=2, seed=syn.BASE_SEED + 64, mixed=True),   # coarsest C1
     "c48": syn.config("c48"),
 }
 
