@@ -11,8 +11,9 @@ Test infrastructure only.  Follows Maynard, Melvin & Mueller (arXiv 2002.00756):
   with face area A_f, cell volume V_i, centre distance d_f and background factor
   g_f = (g_i + g_j)/2 (so V_i a_{i,f} = V_j a_{j,f}: flux antisymmetry).  The terms
   scale as CFL_h^2 horizontally and CFL_v^2 vertically (Eq. DH_ratios).  No flux passes
-  the bottom and top.  For the mixed system the vertical coefficients carry the factor
-  mu_f = 1 / (lumped velocity mass) of their face (Sec. 3.4, Step 1a).
+  the bottom and top.  For the mixed system every coefficient carries the factor
+  mu_f = 1 / (lumped velocity mass) of its face (Sec. 3.4, Step 1a): ``mu`` on the vertical
+  faces, ``mu_h`` (per cell side E, W, N, S) on the horizontal ones.
 * Sec. 3.6, Eq. jacobi: H_z-hat keeps, per column, the vertical couplings and the full
   diagonal of H; one block-Jacobi iteration is x <- x + omega H_z-hat^{-1} (b - H x),
   the tridiagonal solve done per column with the Thomas algorithm.
@@ -34,7 +35,8 @@ class Level:
     a_dn[k, c]    coefficient to cell (k-1, c); 0 on the bottom level
     """
 
-    def __init__(self, mesh: Mesh, g: np.ndarray, cs_dt: float, mu: np.ndarray | None = None):
+    def __init__(self, mesh: Mesh, g: np.ndarray, cs_dt: float, mu: np.ndarray | None = None,
+                 mu_h: np.ndarray | None = None):
         self.mesh = mesh
         nlev, ncol = mesh.nlev, mesh.ncol
         g = np.asarray(g, dtype=np.float64).reshape(nlev, ncol)
@@ -42,13 +44,16 @@ class Level:
         if mu is None:
             mu = np.ones((nlev + 1, ncol))
         self.mu = np.asarray(mu, dtype=np.float64).reshape(nlev + 1, ncol)
+        if mu_h is None:
+            mu_h = np.ones((4, ncol))
+        self.mu_h = np.asarray(mu_h, dtype=np.float64).reshape(4, ncol)
         c2 = cs_dt * cs_dt
         self.a_h = np.empty((4, nlev, ncol))
         for d in range(4):
             nb = mesh.nbr[d]
             gf = 0.5 * (g + g[:, nb])
             # A_f / V_i = edge_length * dz / (area * dz): the layer depth cancels
-            self.a_h[d] = c2 * gf * mesh.edge_len[d][None, :] / (
+            self.a_h[d] = c2 * gf * self.mu_h[d][None, :] * mesh.edge_len[d][None, :] / (
                 mesh.area[None, :] * mesh.centre_dist[d][None, :])
         self.a_up = np.zeros((nlev, ncol))
         self.a_dn = np.zeros((nlev, ncol))

@@ -26,8 +26,26 @@ Test infrastructure only.  Follows Maynard, Melvin & Mueller (arXiv 2002.00756):
       B   = r_p - D M-ring^{-1} r_u                         (Eq. helmholtz right side)
       Pi' ~ H^{-1} B,  H = I - D M-ring^{-1} G             (Eq. helmholtz_operator)
       u'  = M-ring^{-1} (r_u - G Pi')                      (Eq. eliminate_u)
-  H is the Helmholtz operator of ``helmholtz.Level`` with the vertical coefficients
+  H is the Helmholtz operator of ``helmholtz.Level`` with the coefficients of every face
   scaled by mu_f = 1 / M-ring_f.
+* Sec. 3.3, Eq. M2muCdef, optional terms of M2^{mu,C} = M2 + tau_u dt (M_mu + M_C):
+  - ``consistent``: the consistent (non-lumped) lowest-order Raviart-Thomas mass M2 in
+    place of its lumped form, on the reference cell (the lumped mass stays 1 per face, the
+    normalisation of this strong form).  Per cell, with every face basis function taken
+    along the cell's own axis (xi for E/W, eta for N/S, up for bottom/top) and unit flux:
+    integral of a basis function with itself 1/3, with the opposite face's 1/6, with a
+    perpendicular one 0; in the vertical the same pattern couples faces kf and kf +- 1.
+  - ``f0`` = tau_u dt 2 Omega: the implicit Coriolis term (M_C)_ij = 2 int v_i . (Omega x
+    v_j) dV in the traditional approximation (only the local vertical component Omega
+    sin(lat) of the rotation, lat at the cell centre, rotation axis = z): per cell
+    F_c = f0 sin(lat_c) times int psi_a . (z x psi_b) = -1/4 for an xi-face a and an
+    eta-face b, +1/4 for an eta-face a and a xi-face b (skew-symmetric, no work done).
+  Both are assembled with the global orientation: a face's basis is the cell-axis basis
+  times tau = +-1, the sign of the face normal (from the lower- to the higher-numbered
+  column) along that axis.  The lumped diagonal M-ring is the row sum of M-bar taken in
+  each cell's own axes (all tau = +1) over the retained unknowns; it equals the literal
+  row sum wherever the global orientation agrees with the cells' axes (everywhere inside
+  a panel) and does not depend on the orientation at panel edges.
 
 Velocity vector layout (the library's convention): [u_h, u_v]; u_h is (nlev, 2 ncol)
 level-major over the horizontal faces of ``Mesh.hfaces`` order; u_v is (nlev+1, ncol),
@@ -37,18 +55,34 @@ from __future__ import annotations
 
 import numpy as np
 
+import scipy.sparse as sp
+
 from .geometry import Mesh
+
+OUTWARD = (1.0, -1.0, 1.0, -1.0)     # sides E, W, N, S: outward normal along +xi, -xi, +eta, -eta
+
+
+def element_matrices():
+    """Per-cell matrices of the horizontal faces E, W, N, S, basis along the cell axes:
+    (consistent mass, Coriolis for unit F).  Reference cell [0,1]^2 (x xi, y eta), basis
+    E: x e_x, W: (1 - x) e_x, N: y e_y, S: (1 - y) e_y."""
+    M = np.array([[1 / 3, 1 / 6, 0, 0], [1 / 6, 1 / 3, 0, 0],
+                  [0, 0, 1 / 3, 1 / 6], [0, 0, 1 / 6, 1 / 3]])
+    C = np.array([[0, 0, -0.25, -0.25], [0, 0, -0.25, -0.25],
+                  [0.25, 0.25, 0, 0], [0.25, 0.25, 0, 0]])
+    return M, C
 
 
 class MixedSystem:
     def __init__(self, mesh: Mesh, g: np.ndarray, cs_dt: float, beta_up: np.ndarray,
-                 beta_dn: np.ndarray, eps: float):
+                 beta_dn: np.ndarray, eps: float, consistent: bool = False, f0: float = 0.0):
         self.mesh = mesh
         nlev, ncol = mesh.nlev, mesh.ncol
         self.nlev, self.ncol = nlev, ncol
         g = np.asarray(g, dtype=np.float64).reshape(nlev, ncol)
         self.cs_dt = cs_dt
         self.L, self.R, side = mesh.hfaces()
+        self._side = side
         self.nhf = len(self.L)
         self.nh = nlev * self.nhf
         self.nv = (nlev + 1) * ncol
@@ -72,10 +106,44 @@ class MixedSystem:
         up_ok[nlev - 1:] = False        # face kf couples to kf+1 only if kf+1 is interior
         dn_ok = interior.copy()
         dn_ok[:2] = False               # face kf couples to kf-1 only if kf-1 is interior
-        self.w_up = eps * np.asarray(beta_up, dtype=np.float64).reshape(nlev + 1, ncol) * up_ok[:, None]
-        self.w_dn = eps * np.asarray(beta_dn, dtype=np.float64).reshape(nlev + 1, ncol) * dn_ok[:, None]
-        self.m_lump = 1.0 + self.w_up + self.w_dn                            # row sums (Sec. 3.4)
+        off = 1.0 / 6.0 if consistent else 0.0
+        self.mv = 2.0 / 3.0 if consistent else 1.0                            # self weight
+        self.w_up = (eps * np.asarray(beta_up, dtype=np.float64).reshape(nlev + 1, ncol) + off) * up_ok[:, None]
+        self.w_dn = (eps * np.asarray(beta_dn, dtype=np.float64).reshape(nlev + 1, ncol) + off) * dn_ok[:, None]
+        self.m_lump = self.mv + self.w_up + self.w_dn                         # row sums (Sec. 3.4)
+        self.m_lump[0] = self.m_lump[nlev] = 1.0                              # identity rows
         self.mu = 1.0 / self.m_lump                                           # (nlev+1, ncol)
+        self._horizontal_mass(consistent, f0)
+
+    def _horizontal_mass(self, consistent: bool, f0: float):
+        """M_h = M2 + tau_u dt M_C on the horizontal faces of one level (level-independent),
+        assembled cell by cell from ``element_matrices``, and its lumped diagonal."""
+        mesh, ncol = self.mesh, self.ncol
+        face_of = np.empty((4, ncol), dtype=np.int64)
+        for f in range(self.nhf):
+            L, R, s = self.L[f], self.R[f], self._side[f]
+            face_of[s, L] = f
+            face_of[mesh.nbr_dir[s, L], R] = f
+        self.face_of = face_of
+        Me, Ce = element_matrices()
+        if not consistent:
+            Me = 0.5 * np.eye(4)            # lumped mass, 1 per face over its two cells
+        self.F = f0 * mesh.centre[:, 2]     # tau_u dt 2 Omega sin(lat) per cell
+        rows, cols, vals = [], [], []
+        m_h = np.zeros(self.nhf)
+        for c in range(ncol):
+            E = Me + self.F[c] * Ce
+            tau = [OUTWARD[s] * (1.0 if self.L[face_of[s, c]] == c else -1.0) for s in range(4)]
+            for a in range(4):
+                m_h[face_of[a, c]] += E[a].sum()            # row sum in the cell's own axes
+                for b in range(4):
+                    if E[a, b] != 0.0:
+                        rows.append(face_of[a, c])
+                        cols.append(face_of[b, c])
+                        vals.append(tau[a] * tau[b] * E[a, b])
+        self.Mh = sp.csr_matrix((vals, (rows, cols)), shape=(self.nhf, self.nhf))
+        self.m_h = m_h
+        self.mu_h = 1.0 / m_h[face_of]                      # (4, ncol) per cell side
 
     # ---- blocks ----
     def split(self, v: np.ndarray):
@@ -106,25 +174,30 @@ class MixedSystem:
         return out
 
     def mass(self, uv: np.ndarray) -> np.ndarray:
-        """M-bar on vertical faces (horizontal faces: identity)."""
+        """M-bar on vertical faces (boundary rows: identity)."""
         y = uv.copy()
+        y[1:-1] *= self.mv
         y[:-1] += self.w_up[:-1] * uv[1:]
         y[1:] += self.w_dn[1:] * uv[:-1]
         return y
+
+    def mass_h(self, uh: np.ndarray) -> np.ndarray:
+        """M_h on the horizontal faces, level by level."""
+        return np.asarray(self.Mh @ uh.T).T
 
     # ---- operator and preconditioner ----
     def apply(self, v: np.ndarray) -> np.ndarray:
         """A_mixed [u; p] (Eq. linear_matrix, reduced lowest-order form)."""
         uh, uv, p = self.split(v)
         gh, gv = self.grad(p)
-        return self.join(uh + gh, self.mass(uv) + gv, p + self.div(uh, uv))
+        return self.join(self.mass_h(uh) + gh, self.mass(uv) + gv, p + self.div(uh, uv))
 
     def precond(self, v: np.ndarray, helmholtz_solve) -> np.ndarray:
         """Approximate Schur complement (Sec. 3.4, Steps 1-3) with a given H^{-1}."""
         ruh, ruv, rp = self.split(v)
-        B = rp - self.div(ruh, ruv / self.m_lump)              # Step 1 (horizontal mass is 1)
+        B = rp - self.div(ruh / self.m_h, ruv / self.m_lump)    # Step 1
         pi = np.asarray(helmholtz_solve(B), dtype=np.float64).reshape(self.nlev, self.ncol)  # Step 2
         gh, gv = self.grad(pi)
-        uh = ruh - gh                                            # Step 3
+        uh = (ruh - gh) / self.m_h                               # Step 3
         uv = (ruv - gv) / self.m_lump
         return self.join(uh, uv, pi)

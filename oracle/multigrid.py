@@ -37,6 +37,20 @@ def restrict_field(fine: Mesh, coarse: Mesh, f: np.ndarray) -> np.ndarray:
     return acc / coarse.area
 
 
+def restrict_side_field(fine: Mesh, coarse: Mesh, f: np.ndarray) -> np.ndarray:
+    """Per-side face field (4, ncol): the edge-length-weighted mean of the two fine faces
+    that make up each coarse face (children q = 2b + a lying on that side)."""
+    ch = fine.children(coarse)
+    f = np.asarray(f, dtype=np.float64).reshape(4, fine.ncol)
+    on_side = ((1, 3), (0, 2), (2, 3), (0, 1))      # E: a = 1, W: a = 0, N: b = 1, S: b = 0
+    out = np.empty((4, coarse.ncol))
+    for d in range(4):
+        w = [fine.edge_len[d][ch[q]] for q in on_side[d]]
+        v = [f[d][ch[q]] for q in on_side[d]]
+        out[d] = (w[0] * v[0] + w[1] * v[1]) / (w[0] + w[1])
+    return out
+
+
 def restrict(fine: Mesh, coarse: Mesh, r: np.ndarray) -> np.ndarray:
     """Restrict(R): dual of injection, b_c = sum_ch V_ch r_ch / V_c (same layer depth)."""
     return restrict_field(fine, coarse, np.asarray(r).reshape(fine.nlev, fine.ncol))
@@ -51,7 +65,7 @@ class Hierarchy:
     """Meshes and rediscretised operators on levels 1..L (index 0 = finest)."""
 
     def __init__(self, n: int, z_if: np.ndarray, radius: float, levels: int, g: np.ndarray,
-                 cs_dt: float, mu: np.ndarray | None = None):
+                 cs_dt: float, mu: np.ndarray | None = None, mu_h: np.ndarray | None = None):
         if n % (1 << (levels - 1)):
             raise ValueError("C_n must be divisible by 2^(L-1)")
         self.meshes = [Mesh(n >> l, z_if, radius) for l in range(levels)]
@@ -64,7 +78,9 @@ class Hierarchy:
                 g = restrict_field(self.meshes[l - 1], m, g)
                 if mu is not None:
                     mu = restrict_field(self.meshes[l - 1], m, mu)
-            self.levels.append(Level(m, g, cs_dt, mu))
+                if mu_h is not None:
+                    mu_h = restrict_side_field(self.meshes[l - 1], m, mu_h)
+            self.levels.append(Level(m, g, cs_dt, mu, mu_h))
 
     @property
     def L(self) -> int:

@@ -39,7 +39,8 @@ def assemble_helmholtz(H: Level) -> sp.csr_matrix:
 
 
 def assemble_mixed(S: MixedSystem) -> sp.csr_matrix:
-    """[[M-bar, G], [D, I]] as one sparse matrix over [u_h, u_v, p]."""
+    """[[M-bar, G], [D, I]] as one sparse matrix over [u_h, u_v, p] (M-bar: M_h on the
+    horizontal faces of every level, the vertical couplings of ``MixedSystem.mass``)."""
     nlev, ncol, nhf = S.nlev, S.ncol, S.nhf
     rows, cols, vals = [], [], []
 
@@ -52,12 +53,16 @@ def assemble_mixed(S: MixedSystem) -> sp.csr_matrix:
     uh = np.arange(S.nh).reshape(nlev, nhf)
     uv = S.nh + np.arange(S.nv).reshape(nlev + 1, ncol)
     pp = S.nu + np.arange(S.np).reshape(nlev, ncol)
-    # velocity rows: horizontal faces
-    put(uh, uh, 1.0)
+    # velocity rows: horizontal faces, M_h on every level
+    Mh = S.Mh.tocoo()
+    for k in range(nlev):
+        put(uh[k][Mh.row], uh[k][Mh.col], Mh.data)
     put(uh, pp[:, S.R], S.kd_h)
     put(uh, pp[:, S.L], -S.kd_h)
     # velocity rows: vertical faces
-    put(uv, uv, 1.0)
+    self_w = np.full((nlev + 1, ncol), S.mv)
+    self_w[0] = self_w[-1] = 1.0                        # boundary faces: identity rows
+    put(uv, uv, self_w)
     put(uv[:-1], uv[1:], S.w_up[:-1])
     put(uv[1:], uv[:-1], S.w_dn[1:])
     put(uv[1:nlev], pp[1:], S.kd_v[1:nlev])
