@@ -364,8 +364,11 @@ def run_mixed(args, cfg, inp, mg, torch, world, rank):
         "metric": f"ms per mixed (u, p) solve to {args.tol:g} rel. residual at {cfg.name.upper()}",
         "value": round(ms_solve, 4), "unit": "ms", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "higher_is_better": False, "dtype": "f64" if args.precision == "fp64" else "f64+f32", "data": "synthetic",
-        "config": {"workload": f"{cfg.name} mixed system (eps = {cfg.eps}), GCR(5) + Schur-complement "
-                               f"{cfg.levels}-level {args.precision} V-cycle", "n": cfg.n, "nlev": cfg.nlev,
+        "config": {"workload": f"{cfg.name} mixed system (eps = {cfg.eps}"
+                               + (", consistent velocity mass" if cfg.consistent_mass else "")
+                               + (f", rotation {cfg.rotation:g}/s" if cfg.rotation else "")
+                               + f"), GCR(5) + Schur-complement {cfg.levels}-level {args.precision} V-cycle",
+                   "n": cfg.n, "nlev": cfg.nlev,
                    "unknowns_u": int(ru.numel()), "unknowns_p": int(rp.numel()),
                    "iters_per_solve": statistics.mean(iters)},
         "roofline": {"bound": "hbm", "kernel": f"{kind}@L{lev}", "achieved": round(byt / (ms * 1e-3) / 1e9, 1),
@@ -398,6 +401,10 @@ def main():
                     help="mixed: the (u, p) solve (GCR + Schur-complement multigrid) on the C48L30 "
                          "mixed workload instead of the headline pressure solve")
     ap.add_argument("--tol", type=float, default=1e-8)
+    ap.add_argument("--consistent-mass", action="store_true",
+                    help="mixed system: consistent RT0 velocity mass instead of the lumped one")
+    ap.add_argument("--rotation", type=float, default=0.0,
+                    help="mixed system: planet angular velocity [1/s] of the implicit Coriolis term")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--profile-solve", action="store_true",
                     help="untimed: one pressure solve limited to --iters GCR iterations (for ncu captures)")
@@ -419,6 +426,9 @@ def main():
     if args.dt is not None or args.levels is not None:
         import dataclasses
         cfg = dataclasses.replace(cfg, dt=args.dt or cfg.dt, levels=args.levels or cfg.levels)
+    if args.consistent_mass or args.rotation:
+        import dataclasses
+        cfg = dataclasses.replace(cfg, consistent_mass=args.consistent_mass, rotation=args.rotation)
     inp = syn.make_inputs(cfg, mixed=args.system == "mixed")
     if args.impl == "reference" and args.system == "mixed":
         if rank == 0:

@@ -19,8 +19,8 @@
  *   (H x)_i = x_i + sum_{faces f of cell i} a_{i,f} (x_i - x_j(f)),
  *   a_{i,f} = (c_s dt)^2 g_f mu_f A_f / (V_i d_f),   g_f = (g_i + g_j) / 2,
  * A_f face area, V_i cell volume, d_f centre distance (great-circle arc horizontally,
- * centre-to-centre height vertically), mu_f = 1 on horizontal faces and 1 / (lumped
- * velocity mass) on vertical faces of the mixed system (1 for the pressure-only system).
+ * centre-to-centre height vertically), mu_f = 1 / (lumped velocity mass of face f) for
+ * the mixed system (1 for the pressure-only system).
  * No flux crosses the surface or the lid.
  *
  * Mesh convention (shared by all vectors): equiangular gnomonic cubed sphere C_n.
@@ -91,13 +91,30 @@ typedef struct {
     int32_t max_iter;            /* Krylov iteration limit */
 } mg_params;
 
-/* mixed-system data (Sec. 3.3-3.4): velocity mass M-bar = I + eps B_w on vertical faces,
- * B_w coupling interior vertical face kf to kf+1 with weight beta_up[kf*ncol+col] and to
- * kf-1 with beta_dn[kf*ncol+col] (only between interior faces). */
+/* mixed-system data (Sec. 3.3-3.4): velocity mass M-bar = M2 + tau_u dt M_C + eps B_w.
+ *   B_w couples interior vertical face kf to kf+1 with weight beta_up[kf*ncol+col] and to
+ *       kf-1 with beta_dn[kf*ncol+col] (only between interior faces; the folded buoyancy
+ *       term of Step 1a);
+ *   M2  is the identity (lumped mass) with consistent = 0; with consistent = 1 the
+ *       consistent lowest-order Raviart-Thomas mass on the reference cell: per cell, with
+ *       each face's basis function along the cell's own axis (xi for E/W, eta for N/S, up
+ *       for bottom/top), 1/3 with itself and 1/6 with the opposite face of the cell; the
+ *       global basis is that times the sign of the face normal along the axis;
+ *   M_C is the implicit Coriolis term of Eq. M2muCdef in the traditional approximation:
+ *       per cell F_c = coriolis_f0 * sin(latitude of the centre, axis z) times -1/4
+ *       between each xi-face (row) and eta-face (column) of the cell and +1/4 between each
+ *       eta-face and xi-face; coriolis_f0 = tau_u dt 2 Omega (0: no rotation).
+ * The Schur-complement preconditioner lumps M-bar to the row sums taken in each cell's
+ * own axes (the literal row sums inside every panel) and scales the Helmholtz coefficient
+ * of every face by 1 / that lumped mass; a coarse horizontal face takes the edge-length-
+ * weighted mean of its two fine faces' factors, a coarse vertical face the area-weighted
+ * mean of its four children's. */
 typedef struct {
     const double* beta_up;       /* HOST, (nlev+1) * ncol */
     const double* beta_dn;       /* HOST, (nlev+1) * ncol */
     double eps;
+    int32_t consistent;          /* 0 lumped (identity) velocity mass, 1 consistent RT0 mass */
+    double coriolis_f0;          /* tau_u dt 2 Omega, dimensionless, |f0| < 1/2 (lumped mass >= 1/2) */
 } mg_mixed;
 
 typedef struct {
@@ -117,7 +134,7 @@ typedef struct mg_handle mg_handle;
  * paragraph before Algorithm 1 and Sec. 5.1 set-up costs) on the current CUDA device.
  *   g      HOST, N background-state factors (cell field layout), g > 0
  *   mixed  NULL for the Helmholtz system alone; otherwise the mixed-system data, which
- *          also scales the vertical Helmholtz coefficients by 1 / lumped mass
+ *          also scales the Helmholtz coefficients by 1 / lumped mass of their faces
  * Meshes with 2 * (nlev + 1) * 6 n^2 >= 2^32 (more than about 2^31 horizontal-face values
  * on the finest level, e.g. n > 2240 at nlev = 70) are rejected with MG_ERR_UNSUPPORTED:
  * the column kernels address a level with 32-bit offsets.

@@ -44,7 +44,7 @@ class _Params(ctypes.Structure):
 
 class _Mixed(ctypes.Structure):
     _fields_ = [("beta_up", ctypes.POINTER(ctypes.c_double)), ("beta_dn", ctypes.POINTER(ctypes.c_double)),
-                ("eps", ctypes.c_double)]
+                ("eps", ctypes.c_double), ("consistent", ctypes.c_int32), ("coriolis_f0", ctypes.c_double)]
 
 
 class _KRec(ctypes.Structure):
@@ -187,7 +187,8 @@ def _check(st: int, what: str):
 def mg_setup(n: int, nlev: int, z_interfaces, g, *, radius: float = 6371.0e3, cs_dt: float = 340.0 * 600.0,
              levels: int = 4, omega: float = 0.8, n_pre: int = 2, n_post: int = 2, n_coarse: int = 4,
              precision: str | int = "fp64", gcr_restart: int = 5, max_iter: int = 200,
-             beta_up=None, beta_dn=None, eps: float = 0.0) -> Handle:
+             beta_up=None, beta_dn=None, eps: float = 0.0, consistent_mass: bool = False,
+             coriolis_f0: float = 0.0) -> Handle:
     """Build the hierarchy on the current CUDA device (see mg_setup in mgsolve.h)."""
     import torch
     torch.cuda.current_device()   # make sure the device context exists
@@ -204,7 +205,7 @@ def mg_setup(n: int, nlev: int, z_interfaces, g, *, radius: float = 6371.0e3, cs
         bu, bup = _host(beta_up, (nlev + 1) * ncol, "beta_up")
         bd, bdp = _host(beta_dn, (nlev + 1) * ncol, "beta_dn")
         keep += [bu, bd]
-        mixed = _Mixed(bup, bdp, eps)
+        mixed = _Mixed(bup, bdp, eps, int(bool(consistent_mass)), coriolis_f0)
     out = ctypes.c_void_p()
     st = lib.mg_setup(ctypes.byref(mesh), ctypes.byref(prm), gp,
                       ctypes.byref(mixed) if mixed is not None else None, ctypes.byref(out))
@@ -221,7 +222,9 @@ def mg_setup_config(cfg, inp: dict, precision: str | int = "fp64", levels: int |
     mixed = cfg.mixed if mixed is None else mixed
     extra = {}
     if mixed:
-        extra = dict(beta_up=inp["beta_up"], beta_dn=inp["beta_dn"], eps=cfg.eps)
+        # Coriolis factor tau_u dt 2 Omega of Eq. M2muCdef, tau_u = 1/2 (Sec. 3.3)
+        extra = dict(beta_up=inp["beta_up"], beta_dn=inp["beta_dn"], eps=cfg.eps,
+                     consistent_mass=cfg.consistent_mass, coriolis_f0=0.5 * cfg.dt * 2.0 * cfg.rotation)
     return mg_setup(cfg.n, cfg.nlev, inp["z_if"], inp["g"], radius=cfg.radius, cs_dt=cfg.cs * cfg.dt,
                     levels=levels or cfg.levels, omega=cfg.omega, n_pre=cfg.n_pre, n_post=cfg.n_post,
                     n_coarse=cfg.n_coarse, precision=precision, gcr_restart=cfg.gcr_restart,

@@ -233,33 +233,44 @@ struct MixedDev {
     const double* kd_v;             // [nlev+1][ncol]
     const double* w_up;             // [nlev+1][ncol] eps beta_up (interior couplings only)
     const double* w_dn;             // [nlev+1][ncol]
-    const double* mlump;            // [nlev+1][ncol] row sums of M-bar
+    const double* rmlump;           // [nlev+1][ncol] 1 / row sums of M-bar
     const double* divv;             // [nlev] c_s dt / dz
+    // horizontal faces: M_h u_f = ms u_f + sum_t wf[t][f] u_cf[t][f] (t < ncf), the same on
+    // every level; lumped to 1 / rmlump_h
+    int ncf;
+    const int32_t* cf;              // [ncf][nfh]
+    const double* wf;               // [ncf][nfh]
+    double ms;                      // horizontal self weight
+    double mv;                      // vertical self weight (interior faces)
+    const double* rmlump_h;         // [nfh] 1 / lumped mass
 };
 
-// (D u)_i, vertical velocities optionally divided by the lumped mass
+// (D u)_i, velocities optionally divided by the lumped mass
 template <bool LUMP>
 __device__ __forceinline__ double div_cell(const MixedDev& M, int k, int c, const double* __restrict__ uh,
                                            const double* __restrict__ uv) {
     const size_t ncol = M.ncol;
     double s = 0.0;
 #pragma unroll
-    for (int d = 0; d < 4; ++d)
-        s += __ldg(M.sdiv + d * ncol + c) * __ldg(uh + (size_t)k * M.nfh + __ldg(M.fof + d * ncol + c));
+    for (int d = 0; d < 4; ++d) {
+        const int f = __ldg(M.fof + d * ncol + c);
+        const double u = __ldg(uh + (size_t)k * M.nfh + f);
+        s += __ldg(M.sdiv + d * ncol + c) * (LUMP ? u * __ldg(M.rmlump_h + f) : u);
+    }
     double v = 0.0;
     if (k + 1 < M.nlev) {
         const size_t o = (size_t)(k + 1) * ncol + c;
-        v += LUMP ? __ldg(uv + o) / __ldg(M.mlump + o) : __ldg(uv + o);
+        v += LUMP ? __ldg(uv + o) * __ldg(M.rmlump + o) : __ldg(uv + o);
     }
     if (k > 0) {
         const size_t o = (size_t)k * ncol + c;
-        v -= LUMP ? __ldg(uv + o) / __ldg(M.mlump + o) : __ldg(uv + o);
+        v -= LUMP ? __ldg(uv + o) * __ldg(M.rmlump + o) : __ldg(uv + o);
     }
     return s + __ldg(M.divv + k) * v;
 }
 
-// velocity rows on horizontal faces: yh = uh + kd (p_R - p_L)   [MODE 0]
-// Step 3 on horizontal faces:         yh = uh - kd (p_R - p_L)   [MODE 1]
+// velocity rows on horizontal faces: yh = M_h uh + kd (p_R - p_L)          [MODE 0]
+// Step 3 on horizontal faces:         yh = (uh - kd (p_R - p_L)) / m_h    [MODE 1, times 1 / m_h]
 template <int MODE>
 __global__ void k_mx_faces_h(MixedDev M, const double* __restrict__ uh, const double* __restrict__ p,
                              double* __restrict__ yh) {
@@ -268,7 +279,15 @@ __global__ void k_mx_faces_h(MixedDev M, const double* __restrict__ uh, const do
     if (f >= M.nfh) return;
     const size_t o = (size_t)k * M.nfh + f, op = (size_t)k * M.ncol;
     const double g = __ldg(M.kd_h + o) * (__ldg(p + op + __ldg(M.faceR + f)) - __ldg(p + op + __ldg(M.faceL + f)));
-    yh[o] = MODE == 0 ? __ldg(uh + o) + g : __ldg(uh + o) - g;
+    if (MODE == 0) {
+        double m = M.ms * __ldg(uh + o);
+        const double* ul = uh + (size_t)k * M.nfh;
+        for (int t = 0; t < M.ncf; ++t)
+            m += __ldg(M.wf + (size_t)t * M.nfh + f) * __ldg(ul + __ldg(M.cf + (size_t)t * M.nfh + f));
+        yh[o] = m + g;
+    } else {
+        yh[o] = (__ldg(uh + o) - g) * __ldg(M.rmlump_h + f);
+    }
 }
 
 // velocity rows on vertical faces: yv = M-bar uv + kd (p_kf - p_kf-1)   [MODE 0]
@@ -286,9 +305,9 @@ __global__ void k_mx_faces_v(MixedDev M, const double* __restrict__ uv, const do
     }
     const double g = __ldg(M.kd_v + o) * (__ldg(p + (size_t)kf * ncol + c) - __ldg(p + (size_t)(kf - 1) * ncol + c));
     if (MODE == 0) {
-        yv[o] = __ldg(uv + o) + __ldg(M.w_up + o) * __ldg(uv + o + ncol) + __ldg(M.w_dn + o) * __ldg(uv + o - ncol) + g;
+        yv[o] = M.mv * __ldg(uv + o) + __ldg(M.w_up + o) * __ldg(uv + o + ncol) + __ldg(M.w_dn + o) * __ldg(uv + o - ncol) + g;
     } else {
-        yv[o] = (__ldg(uv + o) - g) / __ldg(M.mlump + o);
+        yv[o] = (__ldg(uv + o) - g) * __ldg(M.rmlump + o);
     }
 }
 

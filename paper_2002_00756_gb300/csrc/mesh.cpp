@@ -77,6 +77,7 @@ std::string build_hgeom(int n, double radius, HGeom& g) {
     g.n = n;
     g.ncol = ncol;
     g.area.assign(ncol, 0.0);
+    g.sinlat.assign(ncol, 0.0);
     g.nbr.assign(4 * ncol, -1);
     g.nbr_side.assign(4 * ncol, -1);
     g.edge_len.assign(4 * ncol, 0.0);
@@ -99,6 +100,7 @@ std::string build_hgeom(int n, double radius, HGeom& g) {
         g.edge_len[3 * ncol + c] = radius * arc(c00, c10);
         const double xic = xi0 + 0.5 * d, etac = eta0 + 0.5 * d;
         centre[c] = sphere(p, xic, etac);
+        g.sinlat[c] = centre[c].z;
         for (int s = 0; s < 4; ++s) {
             const V3 v = sphere(p, xic + 0.75 * d * di[s], etac + 0.75 * d * dj[s]);
             int pn;
@@ -168,7 +170,7 @@ void level_coefficients(const HGeom& h, const VGeom& v, double cs_dt, LevelCoef&
     c.Tv.assign((size_t)(nlev + 1) * ncol, 0.0);
     for (int f = 0; f < nf; ++f) {
         const int L = h.faceL[f], R = h.faceR[f], s = h.faceSide[f];
-        const double geo = h.edge_len[s * ncol + L] / h.cdist[s * ncol + L];
+        const double geo = h.edge_len[s * ncol + L] / h.cdist[s * ncol + L] * (c.muh.empty() ? 1.0 : c.muh[f]);
         for (int k = 0; k < nlev; ++k) {
             const double gf = 0.5 * (c.g[(size_t)k * ncol + L] + c.g[(size_t)k * ncol + R]);
             c.Th[(size_t)k * nf + f] = c2 * gf * geo;
@@ -193,6 +195,23 @@ void restrict_mean(const HGeom& fine, const HGeom& coarse, int rows, const doubl
             }
             out[(size_t)k * ncc + C] = acc / coarse.area[C];
         }
+    }
+}
+
+void restrict_face_mean(const HGeom& fine, const HGeom& coarse, const double* f, double* out) {
+    // children q = 2b + a of a coarse column lying on each side: E a = 1, W a = 0, N b = 1, S b = 0
+    static const int on_side[4][2] = {{1, 3}, {0, 2}, {2, 3}, {0, 1}};
+    const int ncf = fine.ncol, ncc = coarse.ncol;
+    for (int F = 0; F < 2 * ncc; ++F) {
+        const int C = coarse.faceL[F], s = coarse.faceSide[F];
+        double acc = 0.0, wsum = 0.0;
+        for (int t = 0; t < 2; ++t) {
+            const int ch = child_col(fine.n, C, on_side[s][t]);
+            const double w = fine.edge_len[s * ncf + ch];
+            acc += w * f[fine.face_of[s * ncf + ch]];
+            wsum += w;
+        }
+        out[F] = acc / wsum;
     }
 }
 

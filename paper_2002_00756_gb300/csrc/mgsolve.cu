@@ -697,6 +697,56 @@ struct DeviceGuard {
     }
 };
 
+// Horizontal-face velocity mass M_h = M2 + tau_u dt M_C of the mixed system (level-
+// independent): the self weight, up to 6 couplings per face (the opposite face in each of
+// its two cells, then the two perpendicular faces in each) and the lumped diagonal.
+struct HMass {
+    int ncf = 0;                  // couplings per face (0 or 6)
+    double ms = 1.0;              // self weight (2/3 consistent, 1 lumped)
+    std::vector<int32_t> cf;      // [6][nfh] coupled face
+    std::vector<double> wf;       // [6][nfh] its weight
+    std::vector<double> mlump;    // [nfh] row sums in the cells' own axes
+};
+
+void horizontal_mass(const mg::HGeom& G, bool consistent, double f0, HMass& hm) {
+    const int ncol = G.ncol, nfh = 2 * ncol;
+    const double outward[4] = {1.0, -1.0, 1.0, -1.0};   // E, W, N, S along +xi, -xi, +eta, -eta
+    hm.ms = consistent ? 2.0 / 3.0 : 1.0;
+    hm.ncf = (consistent || f0 != 0.0) ? 6 : 0;
+    hm.mlump.assign(nfh, 0.0);
+    hm.cf.assign((size_t)hm.ncf * nfh, 0);
+    hm.wf.assign((size_t)hm.ncf * nfh, 0.0);
+    // sign of the normal of face (side s of column c) along the cell's axis
+    auto tau = [&](int c, int s) {
+        const int f = G.face_of[s * ncol + c];
+        return outward[s] * (G.faceL[f] == c ? 1.0 : -1.0);
+    };
+    for (int f = 0; f < nfh; ++f) {
+        const int cells[2] = {G.faceL[f], G.faceR[f]};
+        const int sides[2] = {G.faceSide[f], G.nbr_side[G.faceSide[f] * ncol + G.faceL[f]]};
+        double lump = 0.0;
+        for (int e = 0; e < 2; ++e) {
+            const int c = cells[e], a = sides[e];
+            const bool xi = a < 2;
+            const double Fc = f0 * G.sinlat[c], ta = tau(c, a);
+            // element row sum: 1/3 + 1/6 (or the lumped 1/2) and -+ 2 F_c / 4
+            lump += 0.5 + (xi ? -0.5 : 0.5) * Fc;
+            if (hm.ncf == 0) continue;
+            const int b = a ^ 1;   // opposite side
+            hm.cf[(size_t)e * nfh + f] = G.face_of[b * ncol + c];
+            hm.wf[(size_t)e * nfh + f] = consistent ? ta * tau(c, b) / 6.0 : 0.0;
+            const int p0 = xi ? 2 : 0;   // perpendicular sides
+            for (int t = 0; t < 2; ++t) {
+                const int bp = p0 + t;
+                const size_t slot = (size_t)(2 + 2 * e + t) * nfh + f;
+                hm.cf[slot] = G.face_of[bp * ncol + c];
+                hm.wf[slot] = ta * tau(c, bp) * Fc * (xi ? -0.25 : 0.25);
+            }
+        }
+        hm.mlump[f] = lump;
+    }
+}
+
 mg_status setup_impl(mg_handle* h, const mg_mesh* mesh, const mg_params* prm, const double* g,
                      const mg_mixed* mixed) {
     const int L = prm->levels, n = mesh->n, nlev = mesh->nlev;
@@ -722,26 +772,37 @@ mg_status setup_impl(mg_handle* h, const mg_mesh* mesh, const mg_params* prm, co
     for (size_t i = 0; i < N0; ++i)
         if (!(g[i] > 0.0) || !std::isfinite(g[i])) return MG_ERR_ARG;
     co[0].mu.assign(NV0, 1.0);
-    std::vector<double> w_up, w_dn, mlump;
+    std::vector<double> w_up, w_dn;
+    HMass hm;
+    double mv = 1.0;
     if (mixed) {
+        // vertical faces: consistent mass 2/3 on the face and 1/6 to the interior faces
+        // above and below, plus eps B_w; lumped to the row sums
+        const double off = mixed->consistent ? 1.0 / 6.0 : 0.0;
+        mv = mixed->consistent ? 2.0 / 3.0 : 1.0;
         w_up.assign(NV0, 0.0);
         w_dn.assign(NV0, 0.0);
-        mlump.assign(NV0, 1.0);
         for (int kf = 1; kf < nlev; ++kf) {
             for (int c = 0; c < ncol0; ++c) {
                 const size_t o = (size_t)kf * ncol0 + c;
-                if (kf + 1 <= nlev - 1) w_up[o] = mixed->eps * mixed->beta_up[o];
-                if (kf - 1 >= 1) w_dn[o] = mixed->eps * mixed->beta_dn[o];
-                mlump[o] = 1.0 + w_up[o] + w_dn[o];
-                co[0].mu[o] = 1.0 / mlump[o];
+                if (kf + 1 <= nlev - 1) w_up[o] = mixed->eps * mixed->beta_up[o] + off;
+                if (kf - 1 >= 1) w_dn[o] = mixed->eps * mixed->beta_dn[o] + off;
+                co[0].mu[o] = 1.0 / (mv + w_up[o] + w_dn[o]);   // 1 / row sum
             }
         }
+        horizontal_mass(hg[0], mixed->consistent != 0, mixed->coriolis_f0, hm);
+        co[0].muh.resize(hm.mlump.size());
+        for (size_t f = 0; f < hm.mlump.size(); ++f) co[0].muh[f] = 1.0 / hm.mlump[f];
     }
     for (int l = 1; l < L; ++l) {
         co[l].g.resize((size_t)nlev * hg[l].ncol);
         co[l].mu.resize((size_t)(nlev + 1) * hg[l].ncol);
         mg::restrict_mean(hg[l - 1], hg[l], nlev, co[l - 1].g.data(), co[l].g.data());
         mg::restrict_mean(hg[l - 1], hg[l], nlev + 1, co[l - 1].mu.data(), co[l].mu.data());
+        if (!co[l - 1].muh.empty()) {
+            co[l].muh.resize(2 * (size_t)hg[l].ncol);
+            mg::restrict_face_mean(hg[l - 1], hg[l], co[l - 1].muh.data(), co[l].muh.data());
+        }
     }
     for (int l = 0; l < L; ++l) mg::level_coefficients(hg[l], vg, mesh->cs_dt, co[l]);
     // upload
@@ -839,8 +900,8 @@ mg_status setup_impl(mg_handle* h, const mg_mesh* mesh, const mg_params* prm, co
                 const double sgn = (G.faceL[f] == col) ? 1.0 : -1.0;
                 sdiv[(size_t)sd * ncol0 + col] = sgn * c * G.edge_len[sd * ncol0 + col] / G.area[col];
             }
-        int32_t *fL, *fR;
-        double *dkd_h, *dkd_v, *dsdiv, *dwu, *dwd, *dml, *ddivv;
+        int32_t *fL, *fR, *dcf = nullptr;
+        double *dkd_h, *dkd_v, *dsdiv, *dwu, *dwd, *dml, *ddivv, *dwf = nullptr, *dmlh;
         TRY(upload(h, &fL, G.faceL));
         TRY(upload(h, &fR, G.faceR));
         TRY(upload(h, &dkd_h, kd_h));
@@ -848,9 +909,15 @@ mg_status setup_impl(mg_handle* h, const mg_mesh* mesh, const mg_params* prm, co
         TRY(upload(h, &dsdiv, sdiv));
         TRY(upload(h, &dwu, w_up));
         TRY(upload(h, &dwd, w_dn));
-        TRY(upload(h, &dml, mlump));
+        TRY(upload(h, &dml, co[0].mu));     // 1 / lumped mass (1 on the boundary faces)
         TRY(upload(h, &ddivv, divv));
-        h->md = mg::MixedDev{ncol0, nlev, nfh, fL, fR, h->lv[0].fof, dsdiv, dkd_h, dkd_v, dwu, dwd, dml, ddivv};
+        TRY(upload(h, &dmlh, co[0].muh));
+        if (hm.ncf > 0) {
+            TRY(upload(h, &dcf, hm.cf));
+            TRY(upload(h, &dwf, hm.wf));
+        }
+        h->md = mg::MixedDev{ncol0, nlev, nfh, fL, fR, h->lv[0].fof, dsdiv, dkd_h, dkd_v, dwu, dwd, dml, ddivv,
+                             hm.ncf, dcf, dwf, hm.ms, mv, dmlh};
         h->nu = (int64_t)nlev * nfh + (int64_t)NV0;
         TRY(dalloc(h, &h->schurB, N0));
         TRY(dalloc(h, &h->mb, (size_t)h->nu + N0));
@@ -931,7 +998,9 @@ mg_status mg_setup(const mg_mesh* mesh, const mg_params* prm, const double* g, c
     if (!std::isfinite(prm->omega) || prm->n_pre < 0 || prm->n_post < 0 || prm->n_coarse < 1) return MG_ERR_ARG;
     if (prm->vcycle_precision < MG_FP64 || prm->vcycle_precision > MG_FP32_BF16COEF) return MG_ERR_ARG;
     if (prm->gcr_restart < 1 || prm->gcr_restart > MG_MAX_RESTART || prm->max_iter < 1) return MG_ERR_ARG;
-    if (mixed && (!mixed->beta_up || !mixed->beta_dn || !std::isfinite(mixed->eps) || mixed->eps < 0.0))
+    if (mixed && (!mixed->beta_up || !mixed->beta_dn || !std::isfinite(mixed->eps) || mixed->eps < 0.0 ||
+                  (mixed->consistent != 0 && mixed->consistent != 1) || !std::isfinite(mixed->coriolis_f0) ||
+                  std::fabs(mixed->coriolis_f0) >= 0.5))
         return MG_ERR_ARG;
     // the column kernels address a level with 32-bit offsets (horizontal faces: 2 kc)
     if (2.0 * (mesh->nlev + 1) * 6.0 * (double)mesh->n * mesh->n >= 4294967296.0) return MG_ERR_UNSUPPORTED;

@@ -9,6 +9,8 @@ All calls go through the C ABI (ctypes binding).  Tolerances:
   * solves: relative error <= 1e-8 against the oracle's reference solution x* (sparse LU
     or GCR to a relative residual of 1e-12 on the assembled matrix).
 """
+import dataclasses
+
 import numpy as np
 import pytest
 
@@ -293,6 +295,13 @@ MIXED = {
     "m4l6": syn.small_config(4, 6, levels=2, seed=syn.BASE_SEED + 21, mixed=True),
     "m2l4": syn.small_config(2, 4, levels=2, seed=syn.BASE_SEED + 64, mixed=True),   # coarsest C1
     "c48": syn.config("c48"),
+    # consistent velocity mass and implicit Coriolis term (Eq. M2muCdef): a strong rotation
+    # (tau_u dt 2 Omega ~ 0.3) on small meshes, the Earth's on C48L30
+    "m4l6f4": syn.small_config(4, 6, levels=2, seed=syn.BASE_SEED + 65, mixed=True,
+                               consistent_mass=True, rotation=5.0e-4),
+    "m2l4f4": syn.small_config(2, 4, levels=2, seed=syn.BASE_SEED + 66, mixed=True,
+                               consistent_mass=True, rotation=5.0e-4),
+    "c48f4": dataclasses.replace(syn.config("c48"), name="c48f4", consistent_mass=True, rotation=7.292e-5),
 }
 
 

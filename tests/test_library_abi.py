@@ -42,15 +42,21 @@ def test_status_strings(lib):
 
 
 def _setup_raw(lib, n=4, nlev=3, levels=2, precision=0, restart=5, max_iter=10, n_coarse=4, g=None,
-               null_mesh=False):
+               null_mesh=False, mixed=None):
     import paper_2002_00756_gb300 as mg
     z = np.linspace(0.0, 3000.0, nlev + 1)
     gg = np.ones(6 * n * n * nlev) if g is None else g
     mesh = mg._Mesh(n, nlev, 6.371e6, 2.04e5, z.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
     prm = mg._Params(levels, 0.8, 2, 2, n_coarse, precision, restart, max_iter)
     out = ctypes.c_void_p()
+    mx = None
+    if mixed is not None:
+        beta = np.zeros(6 * n * n * (nlev + 1))
+        bp = beta.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+        mx = mg._Mixed(bp, bp, mixed.get("eps", 0.05), mixed.get("consistent", 0), mixed.get("f0", 0.0))
     st = lib.mg_setup(None if null_mesh else ctypes.byref(mesh), ctypes.byref(prm),
-                      gg.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), None, ctypes.byref(out))
+                      gg.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                      None if mx is None else ctypes.byref(mx), ctypes.byref(out))
     return st, out
 
 
@@ -64,6 +70,10 @@ def _setup_raw(lib, n=4, nlev=3, levels=2, precision=0, restart=5, max_iter=10, 
     dict(n_coarse=0),
     dict(nlev=0),
     dict(null_mesh=True),
+    dict(mixed=dict(eps=-1.0)),
+    dict(mixed=dict(consistent=2)),
+    dict(mixed=dict(f0=0.5)),             # |tau_u dt 2 Omega| < 1/2 keeps the lumped mass >= 1/2
+    dict(mixed=dict(f0=float("nan"))),
 ])
 def test_setup_rejects_bad_arguments_on_the_host(lib, kw):
     st, out = _setup_raw(lib, **kw)
