@@ -14,6 +14,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <type_traits>
+
 namespace mg {
 
 template <typename T, typename C>
@@ -109,16 +111,17 @@ __global__ void __launch_bounds__(256) k_apply(Lvl<T, C> L, const X* __restrict_
 // One block-Jacobi sweep (Eq. jacobi): x_out = x + omega Hz^{-1} (b - H x).
 //
 // Two threads per column solve its tridiagonal system from both ends (a twisted
-// factorisation): lanes 0-15 of a warp take the lower half of 16 columns and eliminate
-// upwards from the surface, lanes 16-31 take the upper half of the same columns and
-// eliminate downwards from the lid.  With the coupling to the already-eliminated
+// factorisation): the first half of a block's warps take the lower halves of its columns
+// (32 consecutive columns per warp) and eliminate upwards from the surface, the second
+// half take the upper halves of the same columns and eliminate downwards from the lid, so
+// every copy and load of a warp touches one level.  With the coupling to the already-eliminated
 // neighbour a_prev and to the next one a_next, every step is
 //     m = a_prev / p_prev,  q = s + m q_prev,  p = q + a_next,  y = r + m y_prev
 // (s = 1 + horizontal coefficients: pivots are sums of positive terms).  The two halves
 // meet at rows h-1 and h; their 2x2 system
 //     [p_A  -a_A] [d_A]   [y_A]
 //     [-a_B  p_B] [d_B] = [y_B],   det = q_A p_B + a_A q_B  (no cancellation)
-// is solved by both lanes after a shuffle, then each half back-substitutes towards its
+// is solved by both threads after an exchange through shared memory, then each half back-substitutes towards its
 // end: d_i = y_i/p_i + e_i d_{i+1}, e_i = a_next/p_i, out_i = x_i + omega d_i.  The back
 // substitution runs directly on the output,
 //     out_i = w_i + e_i out_{i+1},   w_i = x_i + omega y_i/p_i - e_i x_{i+1},
@@ -129,10 +132,10 @@ __global__ void __launch_bounds__(256) k_apply(Lvl<T, C> L, const X* __restrict_
 // Latency hiding: the streams first met in DRAM (the next iterate of the own column, b,
 // the E and N faces and the vertical face ahead) are copied DEEP steps ahead into a
 // per-thread shared-memory ring with asynchronous copies (cp.async via the CUDA pipeline
-// primitives), so they occupy no registers while in flight.  The 16 lanes of a half-warp
-// hold 16 consecutive columns at the same level, so the E and W neighbour iterates are the
+// primitives), so they occupy no registers while in flight.  The lanes of a warp hold
+// consecutive columns at the same level, so the E and W neighbour iterates are the
 // adjacent lanes' own values (warp shuffles) and the W face is the left lane's staged E face
-// (shared memory); only where a neighbour is not the adjacent column (ends of the 16-lane
+// (shared memory); only where a neighbour is not the adjacent column (ends of the lane
 // group, panel edges) is it loaded.  Those loads, the N and S neighbours, the S face and the
 // prolongation terms run SHAL steps ahead in a register ring; 1/dz comes from a per-block
 // shared table.  Both rings are indexed statically: the step loop is unrolled by DEEP.
@@ -156,6 +159,12 @@ struct SweepShal {
 #endif
 #ifndef MG_SWEEP_BF16_PAIRS
 #define MG_SWEEP_BF16_PAIRS 1
+#endif
+// 1: the first half of a block's warps take the lower halves of its columns and the second
+// half the upper halves (32 columns per warp, blocks of a multiple of 64 threads); 0: lanes
+// 0-15 and 16-31 of every warp take the two halves of the same 16 columns
+#ifndef MG_SWEEP_WARP_HALVES
+#define MG_SWEEP_WARP_HALVES 1
 #endif
 template <typename T, typename C, int MODE, typename X, typename B, typename O, bool BCOPY, int DEEP, int SHAL>
 __global__ void __launch_bounds__(MG_SWEEP_BLOCK, 4) k_sweep(Lvl<T, C> L, const X* __restrict__ x, const T* __restrict__ xc,
@@ -188,8 +197,16 @@ __global__ void __launch_bounds__(MG_SWEEP_BLOCK, 4) k_sweep(Lvl<T, C> L, const 
     for (int k = threadIdx.x; k < nlev; k += bd) srdz[k] = __ldg(L.rdz + k);
     __syncthreads();
     const int lane = threadIdx.x & 31;
+#if MG_SWEEP_WARP_HALVES
+    const int nwh = bd >> 6;                       // warps per half
+    const bool upper = (threadIdx.x >> 5) >= nwh;
+    const int c_raw = blockIdx.x * (bd >> 1) + ((threadIdx.x >> 5) - (upper ? nwh : 0)) * 32 + lane;
+    const int g = lane, glast = 31;                // lanes holding consecutive columns
+#else
     const bool upper = lane >= 16;
     const int c_raw = blockIdx.x * (bd >> 1) + (threadIdx.x >> 5) * 16 + (lane & 15);
+    const int g = lane & 15, glast = 15;
+#endif
     const bool active = c_raw < L.ncol;
     const int c = active ? c_raw : L.ncol - 1;
     const int nsteps = upper ? nlev - hsteps : hsteps;
@@ -211,9 +228,8 @@ __global__ void __launch_bounds__(MG_SWEEP_BLOCK, 4) k_sweep(Lvl<T, C> L, const 
         for (int s = 0; s < 4; ++s) pn[s] = parent_col(nb[s], L.n);
     }
     const T rA = __ldg(L.rA + c);
-    // E / W neighbours that are the adjacent lanes of the 16-lane group
-    const int g = lane & 15;
-    const bool shE = g != 15 && nb[0] == c + 1;
+    // E / W neighbours that are the adjacent lanes of the group
+    const bool shE = g != glast && nb[0] == c + 1;
     const bool shW = g != 0 && nb[1] == c - 1;
     // the W face is the left lane's E face when it is the same face
     const bool shWf = ASYNC_C && shW && fo[1] == __ldg(L.fof + (c > 0 ? c - 1 : 0));
@@ -388,9 +404,22 @@ __global__ void __launch_bounds__(MG_SWEEP_BLOCK, 4) k_sweep(Lvl<T, C> L, const 
     }
     __pipeline_wait_prior(0);
     // interface rows h-1 (lower half) and h (upper half)
+#if MG_SWEEP_WARP_HALVES
+    // through shared memory (the ring, free once every warp has left it) from the thread
+    // tid ^ (bd / 2) that holds the other half of the column
+    __syncthreads();
+    T* xch = reinterpret_cast<T*>(smem_raw);
+    xch[tid] = q;
+    xch[bd + tid] = y;
+    xch[2 * bd + tid] = anext;
+    __syncthreads();
+    const int pt = tid ^ (bd >> 1);
+    const T qo = xch[pt], yo = xch[bd + pt], ao = xch[2 * bd + pt];
+#else
     const T qo = __shfl_xor_sync(0xffffffffu, q, 16);
     const T yo = __shfl_xor_sync(0xffffffffu, y, 16);
     const T ao = __shfl_xor_sync(0xffffffffu, anext, 16);
+#endif
     T dlt;
     if (nlev - hsteps == 0) {
         dlt = y * ip;   // a single level: nothing above, anext = 0
@@ -571,6 +600,117 @@ __global__ void __launch_bounds__(128) k_resid_restrict16(Lvl<T, C> L, const X* 
             }
         }
     }
+}
+
+// The same residual and restriction for FP32 levels with the own column's streams (b, the
+// iterate one level up, the E and N faces and the vertical face above) copied DEEP levels
+// ahead into a per-thread shared-memory ring by asynchronous 4-byte copies, which hold no
+// registers while in flight; the neighbour iterates, the W and S faces and 1/dz stay in a
+// SHAL-deep register ring.  Same warp layout and arithmetic order as k_resid_restrict16.
+template <int DEEP, int SHAL>
+__global__ void __launch_bounds__(128) k_resid_restrict16a(Lvl<float, float> L, const float* __restrict__ x,
+                                                            const float* __restrict__ b,
+                                                            const float* __restrict__ w, float* __restrict__ bc,
+                                                            int ncol_c, int kchunk) {
+    static_assert(DEEP % SHAL == 0, "ring lengths");
+    __shared__ float ring[5][DEEP][128];   // b, x one level up, E face, N face, vertical face above
+    const int n = L.n, nc = n >> 1, tiles = n >> 4;
+    const int warp = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int nwarps = 6 * nc * tiles;   // (panel, coarse row, tile)
+    const int lane = threadIdx.x & 31, tid = threadIdx.x;
+    const bool valid = warp < nwarps;
+    const int wq = valid ? warp : 0;
+    const int p = wq / (nc * tiles), rem = wq - p * nc * tiles, J = rem / tiles, t = rem - J * tiles;
+    const int rowf = 2 * J + (lane >> 4), i = t * 16 + (lane & 15);
+    const int c = p * n * n + rowf * n + i;
+    const int Cc = p * nc * nc + J * nc + (i >> 1);
+    const int q = ((lane >> 4) << 1) | (i & 1);   // child index 2b + a
+    const size_t ncol = L.ncol, nf = 2 * ncol;
+    const int nlev = L.nlev;
+    const int k0 = blockIdx.y * kchunk;
+    const int k1 = min(nlev, k0 + kchunk);
+    int nb[4], fo[4];
+#pragma unroll
+    for (int s = 0; s < 4; ++s) {
+        nb[s] = __ldg(L.nbr + s * ncol + c);
+        fo[s] = __ldg(L.fof + s * ncol + c);
+    }
+    const float rA = __ldg(L.rA + c);
+    const float wc = __ldg(w + (size_t)q * ncol_c + Cc);
+    const int gl = lane & 15;
+    const bool shE = gl != 15 && nb[0] == c + 1;
+    const bool shW = gl != 0 && nb[1] == c - 1;
+    const bool shWf = shW && fo[1] == __ldg(L.fof + (c > 0 ? c - 1 : 0));
+    auto stage = [&](int k, int slot) {
+        if (k < k1) {
+            const size_t o = (size_t)k * ncol;
+            const bool in = k + 1 < nlev;
+            __pipeline_memcpy_async(&ring[0][slot][tid], b + o + c, 4);
+            __pipeline_memcpy_async(&ring[1][slot][tid], x + (in ? o + ncol : o) + c, 4, in ? 0 : 4);
+            __pipeline_memcpy_async(&ring[2][slot][tid], L.Th + (size_t)k * nf + fo[0], 4);
+            __pipeline_memcpy_async(&ring[3][slot][tid], L.Th + (size_t)k * nf + fo[2], 4);
+            __pipeline_memcpy_async(&ring[4][slot][tid], L.Tv + o + ncol + c, 4);   // row nlev is zero
+        }
+        __pipeline_commit();
+    };
+    struct Lv {
+        float xn[4], tw, ts, rdz;
+    };
+    auto load = [&](int k, Lv& d) {
+        const size_t o = (size_t)k * ncol;
+        if (!shE) d.xn[0] = __ldg(x + o + nb[0]);
+        if (!shW) d.xn[1] = __ldg(x + o + nb[1]);
+        d.xn[2] = __ldg(x + o + nb[2]);
+        d.xn[3] = __ldg(x + o + nb[3]);
+        if (!shWf) d.tw = __ldg(L.Th + (size_t)k * nf + fo[1]);
+        d.ts = __ldg(L.Th + (size_t)k * nf + fo[3]);
+        d.rdz = __ldg(L.rdz + k);
+    };
+#pragma unroll
+    for (int j = 0; j < DEEP; ++j) stage(k0 + j, j);
+    Lv rr[SHAL];
+#pragma unroll
+    for (int j = 0; j < SHAL; ++j)
+        if (k0 + j < k1) load(k0 + j, rr[j]);
+    float xm = k0 == 0 ? 0.f : __ldg(x + (size_t)(k0 - 1) * ncol + c);
+    float x0 = __ldg(x + (size_t)k0 * ncol + c);
+    float tdn = __ldg(L.Tv + (size_t)k0 * ncol + c);
+    for (int kb = k0; kb < k1; kb += DEEP) {
+#pragma unroll
+        for (int j = 0; j < DEEP; ++j) {
+            const int k = kb + j;
+            __pipeline_wait_prior(DEEP - 1);
+            __syncwarp();   // every lane's copies of this slot are complete and visible
+            const float bk = ring[0][j][tid], xp = ring[1][j][tid], te = ring[2][j][tid], tn = ring[3][j][tid],
+                        tup = ring[4][j][tid];
+            __syncwarp();   // reads of the slot are done before it is refilled
+            stage(k + DEEP, j);
+            if (k < k1) {   // uniform over the block
+                const Lv d = rr[j % SHAL];
+                if (k + SHAL < k1) load(k + SHAL, rr[j % SHAL]);
+                const float twl = __shfl_up_sync(0xffffffffu, te, 1);
+                const float xEl = __shfl_down_sync(0xffffffffu, x0, 1);
+                const float xWl = __shfl_up_sync(0xffffffffu, x0, 1);
+                const float tw = shWf ? twl : d.tw;
+                const float xE = shE ? xEl : d.xn[0];
+                const float xW = shW ? xWl : d.xn[1];
+                float h = te * (x0 - xE);
+                h += tw * (x0 - xW);
+                h += tn * (x0 - d.xn[2]);
+                h += d.ts * (x0 - d.xn[3]);
+                float r = bk;
+                r -= x0 + (rA * h + d.rdz * (tup * (x0 - xp) + tdn * (x0 - xm)));
+                xm = x0;
+                x0 = xp;
+                tdn = tup;
+                float v = wc * r;
+                v += __shfl_xor_sync(0xffffffffu, v, 1);
+                v += __shfl_xor_sync(0xffffffffu, v, 16);
+                if (valid && (lane & 17) == 0) bc[(size_t)k * ncol_c + Cc] = v;
+            }
+        }
+    }
+    __pipeline_wait_prior(0);
 }
 
 // x_out[k][c] = (ZB ? 0 : x[k][c]) + xc[k][parent(c)]  (Eq. prolongation, natural injection)

@@ -10,6 +10,7 @@
 #include <mutex>
 #include <new>
 #include <string>
+#include <type_traits>
 #include <utility>
 #include <vector>
 
@@ -34,6 +35,18 @@
 #endif
 #ifndef MG_RESTRICT_BIG_NCOL
 #define MG_RESTRICT_BIG_NCOL 100000
+#endif
+#ifndef MG_RESTRICT_ASYNC
+#define MG_RESTRICT_ASYNC 1          // FP32 levels: own-column streams through a copy ring
+#endif
+#ifndef MG_RESTRICT_ASYNC_NCOL
+#define MG_RESTRICT_ASYNC_NCOL 40000 // smaller levels: the register ring alone is as fast
+#endif
+#ifndef MG_RESTRICT_DEEP
+#define MG_RESTRICT_DEEP 4
+#endif
+#ifndef MG_RESTRICT_ASHAL
+#define MG_RESTRICT_ASHAL 2
 #endif
 #ifndef MG_RESTRICT_SHAL
 #define MG_RESTRICT_SHAL 2
@@ -294,8 +307,14 @@ mg_status launch_sweep(mg_handle* h, int lev, const Lvl<T, C>& L, const X* x, co
         2 * (size_t)hsteps * sizeof(T);
     const size_t per_block = (size_t)L.nlev * sizeof(T);   // the 1/dz table
     int bd = sweep_block(2 * L.ncol);
-    const int cap = (int)((SWEEP_SMEM_MAX - per_block) / per_thread) / 32 * 32;
-    if (cap < 32) return MG_ERR_UNSUPPORTED;
+#if MG_SWEEP_WARP_HALVES
+    constexpr int BQ = 64;   // the halves of a column lie in different warps
+#else
+    constexpr int BQ = 32;
+#endif
+    const int cap = (int)((SWEEP_SMEM_MAX - per_block) / per_thread) / BQ * BQ;
+    if (cap < BQ) return MG_ERR_UNSUPPORTED;
+    if (bd < BQ) bd = BQ;
     if (bd > cap) bd = cap;
     const size_t smem = per_thread * bd + per_block;
     // ring lengths per iterate source (measured at C192L70): a prolongation sweep with a fine
@@ -326,8 +345,20 @@ mg_status launch_restrict(mg_handle* h, int lev, const Lvl<T, C>& L, const X* x,
         // chunks (fewer prologues); smaller levels need the threads of short chunks
         const int kc = L.ncol >= MG_RESTRICT_BIG_NCOL ? MG_RESTRICT_KCHUNK_BIG : MG_RESTRICT_KCHUNK;
         const dim3 grid((warps + 3) / 4, (L.nlev + kc - 1) / kc);
-        mg::k_resid_restrict16<T, C, XZERO, X, B, O, MG_RESTRICT_SHAL><<<grid, 128, 0, s>>>(L, x, b, w, bc, ncol_c,
-                                                                                           kc);
+        constexpr bool ASYNC = MG_RESTRICT_ASYNC && !XZERO && std::is_same<T, float>::value &&
+                               std::is_same<C, float>::value && std::is_same<X, float>::value &&
+                               std::is_same<B, float>::value && std::is_same<O, float>::value;
+        bool async_done = false;
+        if constexpr (ASYNC) {
+            if (L.ncol >= MG_RESTRICT_ASYNC_NCOL) {
+                mg::k_resid_restrict16a<MG_RESTRICT_DEEP, MG_RESTRICT_ASHAL><<<grid, 128, 0, s>>>(L, x, b, w, bc,
+                                                                                                 ncol_c, kc);
+                async_done = true;
+            }
+        }
+        if (!async_done)
+            mg::k_resid_restrict16<T, C, XZERO, X, B, O, MG_RESTRICT_SHAL><<<grid, 128, 0, s>>>(L, x, b, w, bc,
+                                                                                               ncol_c, kc);
         CK(cudaGetLastError());
         return MG_OK;
     }
