@@ -265,6 +265,52 @@ def run_adjoint(args, cfg, inp, mg, torch, world, rank):
     h.destroy()
 
 
+def run_mixed_adjoint(args, cfg, inp, mg, torch, world, rank):
+    """The differentiable mixed solve: forward (u, p) = A^-1 rhs and backward dL/drhs = A^-T
+    dL/d(u, p) through the torch autograd wrapper, L = <w_u, u> + <w_p, p> (C48L30 by default)."""
+    h = mg.mg_setup_config(cfg, inp, precision=args.precision, mixed=True)
+    ru0 = torch.from_numpy(inp["rhs_u"]).cuda()
+    rp0 = torch.from_numpy(inp["rhs_p"]).cuda()
+    wu = torch.from_numpy(syn.normal(cfg.seed, 98, ru0.numel())).cuda()
+    wp = torch.from_numpy(syn.normal(cfg.seed, 99, rp0.numel())).cuda()
+
+    def step():
+        ru = ru0.clone().requires_grad_(True)
+        rp = rp0.clone().requires_grad_(True)
+        u, p = mg.solve_mixed(h, ru, rp, tol=args.tol)
+        ((wu * u).sum() + (wp * p).sum()).backward()
+        return ru.grad, rp.grad
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with Clocks(0) as clk:
+        e0.record()
+        for _ in range(args.steps):
+            step()
+        e1.record()
+        torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    fwd = mg.mixed_solve(h, ru0, rp0, torch.zeros_like(ru0), torch.zeros_like(rp0), tol=args.tol)
+    adj = mg.mixed_solve_adjoint(h, wu, wp, torch.zeros_like(ru0), torch.zeros_like(rp0), tol=args.tol)
+    line = {
+        "metric": f"ms per forward + backward mixed (u, p) solve (autograd) at {cfg.name.upper()}",
+        "value": round(ms, 4), "unit": "ms", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "higher_is_better": False, "dtype": "f64" if args.precision == "fp64" else "f64+f32", "data": "synthetic",
+        "config": {"workload": f"{cfg.name} mixed system (eps = {cfg.eps}"
+                               + (", consistent velocity mass" if cfg.consistent_mass else "")
+                               + (f", rotation {cfg.rotation:g}/s" if cfg.rotation else "")
+                               + f"), {cfg.levels}-level {args.precision} V-cycle; loss <w, (u, p)>, dL/drhs "
+                                 "by the adjoint solve",
+                   "forward_iters": fwd.iters, "adjoint_iters": adj.iters},
+        "clocks": clk.result,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    h.destroy()
+
+
 ENSEMBLE = [(n, nlev) for n in (32, 40, 48, 64, 80, 96, 112, 128) for nlev in (30, 50, 70)]
 
 
@@ -397,7 +443,8 @@ def main():
                     help="time step in s (default: the workload's, 600 s; 1200 s gives CFL_h ~ 7.9 at C192, "
                          "the paper's regime for the robustness sweep)")
     ap.add_argument("--levels", type=int, default=None, help="multigrid levels (default: the workload's)")
-    ap.add_argument("--system", default="pressure", choices=["pressure", "mixed", "ensemble", "adjoint"],
+    ap.add_argument("--system", default="pressure", choices=["pressure", "mixed", "ensemble", "adjoint",
+                                                             "mixed_adjoint"],
                     help="mixed: the (u, p) solve (GCR + Schur-complement multigrid) on the C48L30 "
                          "mixed workload instead of the headline pressure solve")
     ap.add_argument("--tol", type=float, default=1e-8)
@@ -413,11 +460,11 @@ def main():
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3
     world, rank, local = dist_init()
-    if args.system == "mixed" and args.workload == "c192":
+    if args.system in ("mixed", "mixed_adjoint") and args.workload == "c192":
         args.workload = "c48"
     if args.system == "adjoint" and args.workload == "c192":
         args.workload = "c96"
-    if args.impl == "reference" and args.system in ("ensemble", "adjoint"):
+    if args.impl == "reference" and args.system in ("ensemble", "adjoint", "mixed_adjoint"):
         if rank == 0:
             print(json.dumps({"impl": "reference", "unavailable": "the reference arm times the pressure solve "
                                                                   "only (the headline metric)"}))
@@ -429,7 +476,7 @@ def main():
     if args.consistent_mass or args.rotation:
         import dataclasses
         cfg = dataclasses.replace(cfg, consistent_mass=args.consistent_mass, rotation=args.rotation)
-    inp = syn.make_inputs(cfg, mixed=args.system == "mixed")
+    inp = syn.make_inputs(cfg, mixed=args.system in ("mixed", "mixed_adjoint"))
     if args.impl == "reference" and args.system == "mixed":
         if rank == 0:
             print(json.dumps({"impl": "reference", "unavailable": "the reference arm times the pressure solve "
@@ -458,6 +505,8 @@ def main():
         return run_ensemble(args, mg, torch, world, rank)
     if args.system == "adjoint":
         return run_adjoint(args, cfg, inp, mg, torch, world, rank)
+    if args.system == "mixed_adjoint":
+        return run_mixed_adjoint(args, cfg, inp, mg, torch, world, rank)
 
     if args.profile_solve:
         h = mg.mg_setup_config(cfg, inp, precision=args.precision, mixed=False, max_iter=args.iters)

@@ -237,6 +237,28 @@ mg_status ensemble_pressure_solve(mg_handle* const* handles, int32_t count, cons
 mg_status mixed_apply(mg_handle* h, const double* u, const double* p, double* yu, double* yp,
                       void* stream);
 
+/* [yu; yp] = A^T [u; p], the transposed mixed operator, evaluated as S J A-hat J S^-1 (see
+ * mixed_solve_adjoint).  Uses the handle's mixed workspace: not concurrent with a mixed
+ * solve on the same handle.  u, yu: DEVICE, nu doubles; p, yp: DEVICE, N doubles. */
+mg_status mixed_apply_transpose(mg_handle* h, const double* u, const double* p, double* yu, double* yp,
+                                void* stream);
+
+/* Adjoint of the mixed solve (the backward step of a differentiable mixed_solve): with
+ * g = [g_u; g_p] = dL/d[u; p] for a loss L of the solution of A [u; p] = rhs, computes
+ * lambda = A^-T g = dL/drhs.  The discrete integration by parts of the gradient and
+ * divergence of Sec. 3.3 (W G = -D^T V with face weights W_f = A_f d_f / g_f, A_f the face
+ * area, d_f the centre distance, and V the cell volumes) gives A^T = S J A-hat J S^-1 with
+ * S = diag(W, V), J = diag(I, -I) and A-hat the mixed operator whose velocity mass is
+ * W^-1 M-bar^T W.  So lambda = S J y with A-hat y = J S^-1 g, solved by GCR(gcr_restart) with
+ * the same Schur-complement preconditioner as mixed_solve (its transpose is S J P J S^-1 by
+ * the same identity and the V-symmetry of the V-cycle).  tol applies to the relative
+ * residual of the A-hat system (W and V are of the same size, so it is close to that of
+ * A^T lambda = g); info as for mixed_solve.
+ * g_u, lam_u: DEVICE, nu doubles; g_p, lam_p: DEVICE, N doubles; g and lambda must not
+ * overlap the handle's buffers (any caller-owned arrays qualify). */
+mg_status mixed_solve_adjoint(mg_handle* h, const double* g_u, const double* g_p, double* lam_u, double* lam_p,
+                              double tol, mg_solve_info* info, void* stream);
+
 /* [u; p] = P_mixed [ru; rp], the Schur-complement preconditioner with one V-cycle. */
 mg_status schur_precond(mg_handle* h, const double* ru, const double* rp, double* u, double* p,
                         void* stream);

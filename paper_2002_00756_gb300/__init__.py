@@ -82,6 +82,8 @@ _SIGS = {
     "mg_residual_restrict": [_VP, _I32, _DP, _DP, _DP, _VP],
     "mg_prolong_add": [_VP, _I32, _DP, _DP, _VP],
     "mixed_apply": [_VP, _DP, _DP, _DP, _DP, _VP],
+    "mixed_apply_transpose": [_VP, _DP, _DP, _DP, _DP, _VP],
+    "mixed_solve_adjoint": [_VP, _DP, _DP, _DP, _DP, _D, ctypes.POINTER(_Info), _VP],
     "schur_precond": [_VP, _DP, _DP, _DP, _DP, _VP],
     "mg_profile_start": [_VP, _I32, _I32, _I32],
     "mg_profile_stop": [_VP, ctypes.POINTER(_KRec), _I32, ctypes.POINTER(ctypes.c_int32)],
@@ -332,6 +334,60 @@ def mixed_solve(h: Handle, rhs_u, rhs_p, u, p, tol: float = 1e-8, stream=None) -
     st = load().mixed_solve(h.ptr, _ptr(rhs_u, h.nu, "rhs_u"), _ptr(rhs_p, h.ncell, "rhs_p"),
                             _ptr(u, h.nu, "u"), _ptr(p, h.ncell, "p"), tol, ctypes.byref(info), _stream(stream))
     return _solve_status(st, info, "mixed_solve")
+
+
+def mixed_solve_adjoint(h: Handle, g_u, g_p, lam_u, lam_p, tol: float = 1e-8, stream=None) -> SolveInfo:
+    """[lam_u; lam_p] = A^-T [g_u; g_p] (see mixed_solve_adjoint in mgsolve.h)."""
+    info = _Info()
+    st = load().mixed_solve_adjoint(h.ptr, _ptr(g_u, h.nu, "g_u"), _ptr(g_p, h.ncell, "g_p"),
+                                    _ptr(lam_u, h.nu, "lam_u"), _ptr(lam_p, h.ncell, "lam_p"), tol,
+                                    ctypes.byref(info), _stream(stream))
+    return _solve_status(st, info, "mixed_solve_adjoint")
+
+
+def mixed_apply_transpose(h: Handle, u, p, yu, yp, stream=None):
+    _check(load().mixed_apply_transpose(h.ptr, _ptr(u, h.nu, "u"), _ptr(p, h.ncell, "p"), _ptr(yu, h.nu, "yu"),
+                                        _ptr(yp, h.ncell, "yp"), _stream(stream)), "mixed_apply_transpose")
+
+
+def _mixed_solve_function():
+    import torch
+
+    class MixedSolve(torch.autograd.Function):
+        """[u; p] = A^-1 [rhs_u; rhs_p] with dL/drhs = A^-T dL/d[u; p] (both solves in the library)."""
+
+        @staticmethod
+        def forward(ctx, rhs_u, rhs_p, h, tol):
+            u, p = torch.zeros_like(rhs_u), torch.zeros_like(rhs_p)
+            info = mixed_solve(h, rhs_u.contiguous(), rhs_p.contiguous(), u, p, tol=tol)
+            if not info.converged:
+                raise MGError(info.status, "mixed_solve")
+            ctx.h, ctx.tol = h, tol
+            return u, p
+
+        @staticmethod
+        def backward(ctx, gu, gp):
+            # (autograd materialises an unused output's gradient as zeros)
+            gu, gp = gu.contiguous(), gp.contiguous()
+            lu, lp = torch.zeros_like(gu), torch.zeros_like(gp)
+            info = mixed_solve_adjoint(ctx.h, gu, gp, lu, lp, tol=ctx.tol)
+            if not info.converged:
+                raise MGError(info.status, "mixed_solve_adjoint")
+            return lu, lp, None, None
+
+    return MixedSolve
+
+
+def solve_mixed(h: Handle, rhs_u, rhs_p, tol: float = 1e-8):
+    """Differentiable mixed solve: (u, p) = A^-1 (rhs_u, rhs_p) as a torch operation (float64
+    CUDA tensors); its backward pass is mixed_solve_adjoint."""
+    global _MS
+    if _MS is None:
+        _MS = _mixed_solve_function()
+    return _MS.apply(rhs_u, rhs_p, h, tol)
+
+
+_MS = None
 
 
 def mg_level_apply(h: Handle, level: int, x, y, stream=None):

@@ -243,6 +243,11 @@ struct MixedDev {
     double ms;                      // horizontal self weight
     double mv;                      // vertical self weight (interior faces)
     const double* rmlump_h;         // [nfh] 1 / lumped mass
+    // adjoint: wfT[t][f] = weight of the entry of row cf[t][f] of M_h that points to f (the
+    // rows of M_h^T), and the face weights W_f = A_f d_f / g_f on [u_h, u_v] (area dz / g of
+    // the cell on the surface and lid faces), under which A^T = S J A-hat J S^-1 with S = diag(W, V)
+    const double* wfT;              // [ncf][nfh]
+    const double* Wf;               // [nlev][nfh] then [nlev+1][ncol]
 };
 
 // (D u)_i, velocities optionally divided by the lumped mass
@@ -271,6 +276,7 @@ __device__ __forceinline__ double div_cell(const MixedDev& M, int k, int c, cons
 
 // velocity rows on horizontal faces: yh = M_h uh + kd (p_R - p_L)          [MODE 0]
 // Step 3 on horizontal faces:         yh = (uh - kd (p_R - p_L)) / m_h    [MODE 1, times 1 / m_h]
+// rows of A-hat:                      yh = (W^-1 M_h^T W uh) + kd (p_R - p_L)  [MODE 2]
 template <int MODE>
 __global__ void k_mx_faces_h(MixedDev M, const double* __restrict__ uh, const double* __restrict__ p,
                              double* __restrict__ yh) {
@@ -285,12 +291,23 @@ __global__ void k_mx_faces_h(MixedDev M, const double* __restrict__ uh, const do
         for (int t = 0; t < M.ncf; ++t)
             m += __ldg(M.wf + (size_t)t * M.nfh + f) * __ldg(ul + __ldg(M.cf + (size_t)t * M.nfh + f));
         yh[o] = m + g;
+    } else if (MODE == 2) {
+        const double* ul = uh + (size_t)k * M.nfh;
+        const double* Wl = M.Wf + (size_t)k * M.nfh;
+        double m = 0.0;
+        for (int t = 0; t < M.ncf; ++t) {
+            const int gf = __ldg(M.cf + (size_t)t * M.nfh + f);
+            m += __ldg(M.wfT + (size_t)t * M.nfh + f) * (__ldg(Wl + gf) * __ldg(ul + gf));
+        }
+        yh[o] = (M.ms * __ldg(uh + o) + m / __ldg(Wl + f)) + g;
     } else {
         yh[o] = (__ldg(uh + o) - g) * __ldg(M.rmlump_h + f);
     }
 }
 
 // velocity rows on vertical faces: yv = M-bar uv + kd (p_kf - p_kf-1)   [MODE 0]
+// rows of A-hat: the couplings of M-bar^T (face kf+1's coupling down, face kf-1's up)
+// weighted by W_neighbour / W_kf                                        [MODE 2]
 // Step 3 on vertical faces:         yv = (uv - kd (p_kf - p_kf-1)) / m  [MODE 1]
 template <int MODE>
 __global__ void k_mx_faces_v(MixedDev M, const double* __restrict__ uv, const double* __restrict__ p,
@@ -306,8 +323,32 @@ __global__ void k_mx_faces_v(MixedDev M, const double* __restrict__ uv, const do
     const double g = __ldg(M.kd_v + o) * (__ldg(p + (size_t)kf * ncol + c) - __ldg(p + (size_t)(kf - 1) * ncol + c));
     if (MODE == 0) {
         yv[o] = M.mv * __ldg(uv + o) + __ldg(M.w_up + o) * __ldg(uv + o + ncol) + __ldg(M.w_dn + o) * __ldg(uv + o - ncol) + g;
+    } else if (MODE == 2) {
+        const double* Wv = M.Wf + (size_t)M.nlev * M.nfh;
+        const double m = __ldg(M.w_dn + o + ncol) * (__ldg(Wv + o + ncol) * __ldg(uv + o + ncol)) +
+                         __ldg(M.w_up + o - ncol) * (__ldg(Wv + o - ncol) * __ldg(uv + o - ncol));
+        yv[o] = (M.mv * __ldg(uv + o) + m / __ldg(Wv + o)) + g;
     } else {
         yv[o] = (__ldg(uv + o) - g) * __ldg(M.rmlump + o);
+    }
+}
+
+// [out_u; out_p] = J S^-1 [in_u; in_p] (MULT false) or S J [in_u; in_p] (MULT true), with
+// S = diag(W, V) (V = area dz, the cell volumes) and J = diag(I, -I)
+template <bool MULT>
+__global__ void k_mx_adj_scale(MixedDev M, size_t nu, const double* __restrict__ area, const double* __restrict__ dz,
+                               const double* in_u, const double* in_p, double* out_u, double* out_p) {
+    const size_t np = (size_t)M.nlev * M.ncol;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < nu + np; i += (size_t)gridDim.x * blockDim.x) {
+        if (i < nu) {
+            const double w = __ldg(M.Wf + i);
+            out_u[i] = MULT ? in_u[i] * w : in_u[i] / w;
+        } else {
+            const size_t e = i - nu;
+            const int k = (int)(e / M.ncol), c = (int)(e - (size_t)k * M.ncol);
+            const double v = __ldg(area + c) * __ldg(dz + k);
+            out_p[e] = MULT ? -(in_p[e] * v) : -(in_p[e] / v);
+        }
     }
 }
 

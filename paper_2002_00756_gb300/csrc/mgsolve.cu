@@ -114,13 +114,14 @@ struct mg_handle {
     unsigned int* tickets = nullptr;
     double* host_sc = nullptr;  // pinned
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
-    // one CUDA graph per GCR slot j and system (0 pressure, 1 mixed): the V-cycle, the
+    // one CUDA graph per GCR slot j and system (0 pressure, 1 mixed, 2 the mixed adjoint's
+    // A-hat): the V-cycle, the
     // operator with its sums, the orthogonalisation and the read-back of <r, r>, captured on
     // `cap` the first time and replayed on the caller's stream afterwards
     cudaStream_t cap = nullptr;
     cudaStream_t run = nullptr;   // the handle's stream inside an ensemble solve
     cudaEvent_t evx = nullptr;    // ordering event (no timing)
-    cudaGraphExec_t gexec[2][mg::MAXR] = {};
+    cudaGraphExec_t gexec[3][mg::MAXR] = {};
     bool graphs_off = false;
     int red_grid = 0;
     // mixed
@@ -574,7 +575,7 @@ void capture_graph(mg_handle* h, Body& body, cudaGraphExec_t* out) {
 // the read-back of <r, r>), landed (after a synchronisation: read <r, r>, decide, enqueue the
 // solution update when the cycle ends or the solve stops), end (enqueue the closing event).
 struct GcrRun {
-    int sys = 0;          // 0 pressure, 1 mixed: selects the handle's cached graphs
+    int sys = 0;          // 0 pressure, 1 mixed, 2 mixed adjoint: selects the handle's cached graphs
     size_t n = 0;
     double* x = nullptr;
     double tol = 0.0;
@@ -692,6 +693,30 @@ mg_status mixed_apply_impl(mg_handle* h, const double* u, const double* p, doubl
     mg::k_mx_faces_h<0><<<dim3((M.nfh + bd - 1) / bd, M.nlev), bd, 0, s>>>(M, u, p, yu);
     mg::k_mx_faces_v<0><<<dim3((M.ncol + bd - 1) / bd, M.nlev + 1), bd, 0, s>>>(M, u + nh, p, yu + nh);
     mg::k_mx_cells<0><<<dim3((M.ncol + bd - 1) / bd, M.nlev), bd, 0, s>>>(M, u, u + nh, p, yp);
+    CK(cudaGetLastError());
+    return MG_OK;
+}
+
+// A-hat [u; p]: the mixed operator with its velocity mass replaced by W^-1 M-bar^T W
+mg_status mixed_apply_hat_impl(mg_handle* h, const double* u, const double* p, double* yu, double* yp,
+                               cudaStream_t s) {
+    const mg::MixedDev& M = h->md;
+    const size_t nh = (size_t)M.nlev * M.nfh;
+    const int bd = 128;
+    Prof pr(h, MG_K_MIXED, 0, 8.0 * (3.0 * h->nu + 3.0 * cells(h, 0)), s, 2);
+    mg::k_mx_faces_h<2><<<dim3((M.nfh + bd - 1) / bd, M.nlev), bd, 0, s>>>(M, u, p, yu);
+    mg::k_mx_faces_v<2><<<dim3((M.ncol + bd - 1) / bd, M.nlev + 1), bd, 0, s>>>(M, u + nh, p, yu + nh);
+    mg::k_mx_cells<0><<<dim3((M.ncol + bd - 1) / bd, M.nlev), bd, 0, s>>>(M, u, u + nh, p, yp);
+    CK(cudaGetLastError());
+    return MG_OK;
+}
+
+template <bool MULT>
+mg_status mixed_adj_scale(mg_handle* h, const double* in_u, const double* in_p, double* out_u, double* out_p,
+                          cudaStream_t s) {
+    Prof pr(h, MG_K_DOT, 0, 16.0 * ((double)h->nu + (double)cells(h, 0)), s, MULT ? 1 : 0);
+    mg::k_mx_adj_scale<MULT><<<4 * h->nsm, 256, 0, s>>>(h->md, (size_t)h->nu, h->area0, h->dz, in_u, in_p, out_u,
+                                                          out_p);
     CK(cudaGetLastError());
     return MG_OK;
 }
@@ -931,8 +956,40 @@ mg_status setup_impl(mg_handle* h, const mg_mesh* mesh, const mg_params* prm, co
                 const double sgn = (G.faceL[f] == col) ? 1.0 : -1.0;
                 sdiv[(size_t)sd * ncol0 + col] = sgn * c * G.edge_len[sd * ncol0 + col] / G.area[col];
             }
+        // adjoint: face weights W_f = A_f d_f / g_f and the rows of M_h^T.  The surface and lid
+        // faces are decoupled identity rows, so any weight keeps A^T = S J A-hat J S^-1; they
+        // take area dz / g of their cell, the size of the interior weights (a weight far from
+        // those would let their entries dominate the residual norm of the scaled system)
+        std::vector<double> Wf((size_t)nlev * nfh + NV0, 1.0);
+        for (int col = 0; col < ncol0; ++col) {
+            Wf[(size_t)nlev * nfh + col] = G.area[col] * vg.dz[0] / g[col];
+            Wf[(size_t)nlev * nfh + (size_t)nlev * ncol0 + col] =
+                G.area[col] * vg.dz[nlev - 1] / g[(size_t)(nlev - 1) * ncol0 + col];
+        }
+        for (int f = 0; f < nfh; ++f) {
+            const int Lc = G.faceL[f], Rc = G.faceR[f], sd = G.faceSide[f];
+            const double el = G.edge_len[sd * ncol0 + Lc], dist = G.cdist[sd * ncol0 + Lc];
+            for (int k = 0; k < nlev; ++k)
+                Wf[(size_t)k * nfh + f] =
+                    el * vg.dz[k] * dist / (0.5 * (g[(size_t)k * ncol0 + Lc] + g[(size_t)k * ncol0 + Rc]));
+        }
+        for (int kf = 1; kf < nlev; ++kf)
+            for (int col = 0; col < ncol0; ++col)
+                Wf[(size_t)nlev * nfh + (size_t)kf * ncol0 + col] =
+                    G.area[col] * vg.dzc[kf] /
+                    (0.5 * (g[(size_t)(kf - 1) * ncol0 + col] + g[(size_t)kf * ncol0 + col]));
+        std::vector<double> wfT(hm.wf.size(), 0.0);
+        for (int f = 0; f < nfh; ++f)
+            for (int t = 0; t < hm.ncf; ++t) {
+                const int gf = hm.cf[(size_t)t * nfh + f];
+                int found = -1;
+                for (int u = 0; u < hm.ncf; ++u)
+                    if (hm.cf[(size_t)u * nfh + gf] == f) found = u;
+                if (found < 0) return MG_ERR_ARG;   // the coupling pattern is symmetric by construction
+                wfT[(size_t)t * nfh + f] = hm.wf[(size_t)found * nfh + gf];
+            }
         int32_t *fL, *fR, *dcf = nullptr;
-        double *dkd_h, *dkd_v, *dsdiv, *dwu, *dwd, *dml, *ddivv, *dwf = nullptr, *dmlh;
+        double *dkd_h, *dkd_v, *dsdiv, *dwu, *dwd, *dml, *ddivv, *dwf = nullptr, *dmlh, *dwfT = nullptr, *dWf;
         TRY(upload(h, &fL, G.faceL));
         TRY(upload(h, &fR, G.faceR));
         TRY(upload(h, &dkd_h, kd_h));
@@ -946,9 +1003,11 @@ mg_status setup_impl(mg_handle* h, const mg_mesh* mesh, const mg_params* prm, co
         if (hm.ncf > 0) {
             TRY(upload(h, &dcf, hm.cf));
             TRY(upload(h, &dwf, hm.wf));
+            TRY(upload(h, &dwfT, wfT));
         }
+        TRY(upload(h, &dWf, Wf));
         h->md = mg::MixedDev{ncol0, nlev, nfh, fL, fR, h->lv[0].fof, dsdiv, dkd_h, dkd_v, dwu, dwd, dml, ddivv,
-                             hm.ncf, dcf, dwf, hm.ms, mv, dmlh};
+                             hm.ncf, dcf, dwf, hm.ms, mv, dmlh, dwfT, dWf};
         h->nu = (int64_t)nlev * nfh + (int64_t)NV0;
         TRY(dalloc(h, &h->schurB, N0));
         TRY(dalloc(h, &h->mb, (size_t)h->nu + N0));
@@ -1199,6 +1258,41 @@ mg_status mixed_solve(mg_handle* h, const double* rhs_u, const double* rhs_p, do
         CK(cudaMemcpyAsync(p, h->mx + nu, np * sizeof(double), cudaMemcpyDeviceToDevice, s));
     }
     return st;
+}
+
+mg_status mixed_solve_adjoint(mg_handle* h, const double* g_u, const double* g_p, double* lam_u, double* lam_p,
+                              double tol, mg_solve_info* info, void* stream) {
+    if (!h || !g_u || !g_p || !lam_u || !lam_p || !(tol >= 0.0)) return MG_ERR_ARG;
+    if (!h->mixed) return MG_ERR_UNSUPPORTED;
+    DeviceGuard dg(h->device);
+    cudaStream_t s = S(stream);
+    const size_t nu = (size_t)h->nu, np = cells(h, 0), n = nu + np;
+    // A^T = S J A-hat J S^-1: lambda = S J A-hat^-1 (J S^-1 g), A-hat preconditioned by the
+    // Schur-complement step of A itself (its transpose is S J P J S^-1 as well)
+    TRY(mixed_adj_scale<false>(h, g_u, g_p, h->mb, h->mb + nu, s));
+    auto A = [&](const double* v, double* y, int j, cudaStream_t q) {
+        TRY(mixed_apply_hat_impl(h, v, v + nu, y, y + nu, q));
+        return gcr_sums(h, n, y, j, q);
+    };
+    auto P = [&](const double* r, double* z, cudaStream_t q) { return schur_impl(h, r, r + nu, z, z + nu, q); };
+    const mg_status st = gcr(h, 2, n, h->mb, h->mx, tol, info, s, A, P);
+    if (st == MG_OK || st == MG_ERR_NOT_CONVERGED || st == MG_ERR_BREAKDOWN) {
+        TRY(mixed_adj_scale<true>(h, h->mx, h->mx + nu, lam_u, lam_p, s));
+        CK(cudaStreamSynchronize(s));
+    }
+    return st;
+}
+
+mg_status mixed_apply_transpose(mg_handle* h, const double* u, const double* p, double* yu, double* yp,
+                                void* stream) {
+    if (!h || !u || !p || !yu || !yp || u == yu || p == yp) return MG_ERR_ARG;
+    if (!h->mixed) return MG_ERR_UNSUPPORTED;
+    DeviceGuard dg(h->device);
+    cudaStream_t s = S(stream);
+    const size_t nu = (size_t)h->nu;
+    TRY(mixed_adj_scale<false>(h, u, p, h->mb, h->mb + nu, s));
+    TRY(mixed_apply_hat_impl(h, h->mb, h->mb + nu, h->mx, h->mx + nu, s));
+    return mixed_adj_scale<true>(h, h->mx, h->mx + nu, yu, yp, s);
 }
 
 mg_status mg_level_apply(mg_handle* h, int32_t level, const double* x, double* y, void* stream) {
