@@ -259,6 +259,21 @@ mg_status mixed_apply_transpose(mg_handle* h, const double* u, const double* p, 
 mg_status mixed_solve_adjoint(mg_handle* h, const double* g_u, const double* g_p, double* lam_u, double* lam_p,
                               double tol, mg_solve_info* info, void* stream);
 
+/* Gradient of a loss L of the mixed solution [u; p] = A^-1 rhs with respect to the set-up
+ * inputs of the mixed operator, given lam = [lam_u; lam_p] = A^-T dL/d[u; p] (from
+ * mixed_solve_adjoint): dL/dtheta = -<lam, (dA/dtheta) [u; p]>.  The background factors g
+ * enter A only through the gradient weights kappa_f / d_f = c_s dt (g_i + g_j) / (2 d_f), so
+ *   grad_g[k][c]     = -sum over the six faces f of cell (k, c) of lam_f (p_R(f) - p_L(f)) c_s dt / (2 d_f);
+ * the couplings of B_w enter as eps beta, so
+ *   grad_beta_up[kf][c] = -eps lam_kf u_kf+1,  grad_beta_dn[kf][c] = -eps lam_kf u_kf-1
+ * on the vertical faces whose coupling exists (0 elsewhere).  lam_p is not needed (the
+ * pressure rows hold no set-up input).  Not through the preconditioner: the solution does
+ * not depend on it.
+ * lam_u, u: DEVICE, nu doubles; p, grad_g: DEVICE, N doubles; grad_beta_up, grad_beta_dn:
+ * DEVICE, (nlev+1) * ncol doubles. */
+mg_status mixed_coefficient_gradient(mg_handle* h, const double* lam_u, const double* u, const double* p,
+                                     double* grad_g, double* grad_beta_up, double* grad_beta_dn, void* stream);
+
 /* [u; p] = P_mixed [ru; rp], the Schur-complement preconditioner with one V-cycle. */
 mg_status schur_precond(mg_handle* h, const double* ru, const double* rp, double* u, double* p,
                         void* stream);

@@ -119,3 +119,35 @@ def iterative_reference(A: sp.spmatrix, b: np.ndarray, P, tol: float = 1e-12,
     if res > 10 * tol:
         raise RuntimeError(f"reference solve reached only {res:.3e}")
     return x
+
+
+def mixed_coefficient_gradient(S, x: np.ndarray, lam: np.ndarray, eps: float):
+    """dL/dg, dL/dbeta_up, dL/dbeta_dn for L(x), A(g, beta) x = rhs, given lam = A^-T dL/dx.
+
+    Differentiating A x = rhs gives dL = -<lam, dA x>.  In the mixed operator (Sec. 3.3-3.4)
+    the background factors g enter only the gradient weights kappa_f / d_f = c_s dt g_f / d_f
+    with g_f = (g_i + g_j) / 2 (velocity rows: kd_f (p_R - p_L)), and beta enters the vertical
+    velocity mass as eps beta (row kf, column kf + 1 for beta_up, kf - 1 for beta_dn, between
+    interior faces only).  Returns arrays shaped like g (nlev, ncol) and beta (nlev+1, ncol)."""
+    uh, uv, p = S.split(x)
+    lh, lv, _ = S.split(lam)
+    m = S.mesh
+    nlev, ncol = S.nlev, S.ncol
+    dist = m.centre_dist[S._side, S.L]
+    dg = np.zeros((nlev, ncol))
+    # horizontal faces: d kd / d g_L = d kd / d g_R = c_s dt / (2 dist)
+    gk = -lh * (p[:, S.R] - p[:, S.L]) * (S.cs_dt / (2.0 * dist))[None, :]
+    np.add.at(dg, (slice(None), S.L), gk)
+    np.add.at(dg, (slice(None), S.R), gk)
+    # vertical faces kf = 1 .. nlev-1 between cells kf-1 and kf
+    for kf in range(1, nlev):
+        gv = -lv[kf] * (p[kf] - p[kf - 1]) * S.cs_dt / (2.0 * m.dzc[kf])
+        dg[kf - 1] += gv
+        dg[kf] += gv
+    db_up = np.zeros((nlev + 1, ncol))
+    db_dn = np.zeros((nlev + 1, ncol))
+    for kf in range(1, nlev - 1):        # face kf couples to kf + 1 (both interior)
+        db_up[kf] = -eps * lv[kf] * uv[kf + 1]
+    for kf in range(2, nlev):            # face kf couples to kf - 1 (both interior)
+        db_dn[kf] = -eps * lv[kf] * uv[kf - 1]
+    return dg, db_up, db_dn

@@ -84,6 +84,7 @@ _SIGS = {
     "mixed_apply": [_VP, _DP, _DP, _DP, _DP, _VP],
     "mixed_apply_transpose": [_VP, _DP, _DP, _DP, _DP, _VP],
     "mixed_solve_adjoint": [_VP, _DP, _DP, _DP, _DP, _D, ctypes.POINTER(_Info), _VP],
+    "mixed_coefficient_gradient": [_VP, _DP, _DP, _DP, _DP, _DP, _DP, _VP],
     "schur_precond": [_VP, _DP, _DP, _DP, _DP, _VP],
     "mg_profile_start": [_VP, _I32, _I32, _I32],
     "mg_profile_stop": [_VP, ctypes.POINTER(_KRec), _I32, ctypes.POINTER(ctypes.c_int32)],
@@ -343,6 +344,17 @@ def mixed_solve_adjoint(h: Handle, g_u, g_p, lam_u, lam_p, tol: float = 1e-8, st
                                     _ptr(lam_u, h.nu, "lam_u"), _ptr(lam_p, h.ncell, "lam_p"), tol,
                                     ctypes.byref(info), _stream(stream))
     return _solve_status(st, info, "mixed_solve_adjoint")
+
+
+def mixed_coefficient_gradient(h: Handle, lam_u, u, p, grad_g, grad_beta_up, grad_beta_dn, stream=None):
+    """dL/dg (N), dL/dbeta_up, dL/dbeta_dn ((nlev+1) ncol) from lam_u = (A^-T dL/d(u, p))_u and
+    the solution (u, p); see mixed_coefficient_gradient in mgsolve.h."""
+    nv = (h.nlev + 1) * h.ncol
+    _check(load().mixed_coefficient_gradient(h.ptr, _ptr(lam_u, h.nu, "lam_u"), _ptr(u, h.nu, "u"),
+                                             _ptr(p, h.ncell, "p"), _ptr(grad_g, h.ncell, "grad_g"),
+                                             _ptr(grad_beta_up, nv, "grad_beta_up"),
+                                             _ptr(grad_beta_dn, nv, "grad_beta_dn"), _stream(stream)),
+           "mixed_coefficient_gradient")
 
 
 def mixed_apply_transpose(h: Handle, u, p, yu, yp, stream=None):

@@ -248,6 +248,10 @@ struct MixedDev {
     // the cell on the surface and lid faces), under which A^T = S J A-hat J S^-1 with S = diag(W, V)
     const double* wfT;              // [ncf][nfh]
     const double* Wf;               // [nlev][nfh] then [nlev+1][ncol]
+    // coefficient gradient: d(kappa_f / d_f) / d g_i = c_s dt / (2 d_f) for both cells of f
+    const double* cdh;              // [nfh]      c_s dt / (2 centre distance)
+    const double* cdv;              // [nlev+1]   c_s dt / (2 dzc), 0 on surface and lid
+    double eps;                     // strength of B_w
 };
 
 // (D u)_i, velocities optionally divided by the lumped mass
@@ -350,6 +354,41 @@ __global__ void k_mx_adj_scale(MixedDev M, size_t nu, const double* __restrict__
             out_p[e] = MULT ? -(in_p[e] * v) : -(in_p[e] / v);
         }
     }
+}
+
+// dL/dg_i = -sum over the faces f of cell i of lam_f (p_R(f) - p_L(f)) c_s dt / (2 d_f): the
+// background factors enter the mixed operator only through the gradient weights
+// kappa_f / d_f = c_s dt (g_i + g_j) / (2 d_f).  One thread per cell.
+__global__ void k_mx_grad_g(MixedDev M, const double* __restrict__ lam_u, const double* __restrict__ p,
+                            double* __restrict__ grad_g) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x, k = blockIdx.y;
+    if (c >= M.ncol) return;
+    const size_t ncol = M.ncol, op = (size_t)k * ncol;
+    const double* lh = lam_u + (size_t)k * M.nfh;
+    const double* lv = lam_u + (size_t)M.nlev * M.nfh;
+    double s = 0.0;
+#pragma unroll
+    for (int d = 0; d < 4; ++d) {
+        const int f = __ldg(M.fof + d * ncol + c);
+        s -= lh[f] * (__ldg(p + op + __ldg(M.faceR + f)) - __ldg(p + op + __ldg(M.faceL + f))) * __ldg(M.cdh + f);
+    }
+    if (k >= 1)   // face k below the cell
+        s -= lv[op + c] * (__ldg(p + op + c) - __ldg(p + op - ncol + c)) * __ldg(M.cdv + k);
+    if (k + 1 <= M.nlev - 1)   // face k + 1 above it
+        s -= lv[op + ncol + c] * (__ldg(p + op + ncol + c) - __ldg(p + op + c)) * __ldg(M.cdv + k + 1);
+    grad_g[op + c] = s;
+}
+
+// dL/dbeta_up[kf] = -eps lam_kf u_kf+1 and dL/dbeta_dn[kf] = -eps lam_kf u_kf-1 on the
+// vertical faces whose coupling exists (both faces interior), 0 elsewhere.
+__global__ void k_mx_grad_beta(MixedDev M, const double* __restrict__ lam_v, const double* __restrict__ uv,
+                               double* __restrict__ gup, double* __restrict__ gdn) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x, kf = blockIdx.y;
+    if (c >= M.ncol) return;
+    const size_t ncol = M.ncol, o = (size_t)kf * ncol + c;
+    const int nlev = M.nlev;
+    gup[o] = (kf >= 1 && kf + 1 <= nlev - 1) ? -M.eps * lam_v[o] * uv[o + ncol] : 0.0;
+    gdn[o] = (kf >= 2 && kf <= nlev - 1) ? -M.eps * lam_v[o] * uv[o - ncol] : 0.0;
 }
 
 // pressure rows: yp = p + D u                           [MODE 0]

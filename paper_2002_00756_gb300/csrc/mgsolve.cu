@@ -988,8 +988,12 @@ mg_status setup_impl(mg_handle* h, const mg_mesh* mesh, const mg_params* prm, co
                 if (found < 0) return MG_ERR_ARG;   // the coupling pattern is symmetric by construction
                 wfT[(size_t)t * nfh + f] = hm.wf[(size_t)found * nfh + gf];
             }
+        std::vector<double> cdh(nfh), cdv(nlev + 1, 0.0);
+        for (int f = 0; f < nfh; ++f) cdh[f] = c / (2.0 * G.cdist[G.faceSide[f] * ncol0 + G.faceL[f]]);
+        for (int kf = 1; kf < nlev; ++kf) cdv[kf] = c / (2.0 * vg.dzc[kf]);
         int32_t *fL, *fR, *dcf = nullptr;
-        double *dkd_h, *dkd_v, *dsdiv, *dwu, *dwd, *dml, *ddivv, *dwf = nullptr, *dmlh, *dwfT = nullptr, *dWf;
+        double *dkd_h, *dkd_v, *dsdiv, *dwu, *dwd, *dml, *ddivv, *dwf = nullptr, *dmlh, *dwfT = nullptr, *dWf, *dcdh,
+            *dcdv;
         TRY(upload(h, &fL, G.faceL));
         TRY(upload(h, &fR, G.faceR));
         TRY(upload(h, &dkd_h, kd_h));
@@ -1006,8 +1010,10 @@ mg_status setup_impl(mg_handle* h, const mg_mesh* mesh, const mg_params* prm, co
             TRY(upload(h, &dwfT, wfT));
         }
         TRY(upload(h, &dWf, Wf));
+        TRY(upload(h, &dcdh, cdh));
+        TRY(upload(h, &dcdv, cdv));
         h->md = mg::MixedDev{ncol0, nlev, nfh, fL, fR, h->lv[0].fof, dsdiv, dkd_h, dkd_v, dwu, dwd, dml, ddivv,
-                             hm.ncf, dcf, dwf, hm.ms, mv, dmlh, dwfT, dWf};
+                             hm.ncf, dcf, dwf, hm.ms, mv, dmlh, dwfT, dWf, dcdh, dcdv, mixed->eps};
         h->nu = (int64_t)nlev * nfh + (int64_t)NV0;
         TRY(dalloc(h, &h->schurB, N0));
         TRY(dalloc(h, &h->mb, (size_t)h->nu + N0));
@@ -1281,6 +1287,23 @@ mg_status mixed_solve_adjoint(mg_handle* h, const double* g_u, const double* g_p
         CK(cudaStreamSynchronize(s));
     }
     return st;
+}
+
+mg_status mixed_coefficient_gradient(mg_handle* h, const double* lam_u, const double* u, const double* p,
+                                     double* grad_g, double* grad_beta_up, double* grad_beta_dn, void* stream) {
+    if (!h || !lam_u || !u || !p || !grad_g || !grad_beta_up || !grad_beta_dn) return MG_ERR_ARG;
+    if (!h->mixed) return MG_ERR_UNSUPPORTED;
+    DeviceGuard dg(h->device);
+    cudaStream_t s = S(stream);
+    const mg::MixedDev& M = h->md;
+    const size_t nh = (size_t)M.nlev * M.nfh;
+    const int bd = 128;
+    Prof pr(h, MG_K_DOT, 0, 8.0 * (3.0 * h->nu + 2.0 * cells(h, 0)), s, 3);
+    mg::k_mx_grad_g<<<dim3((M.ncol + bd - 1) / bd, M.nlev), bd, 0, s>>>(M, lam_u, p, grad_g);
+    mg::k_mx_grad_beta<<<dim3((M.ncol + bd - 1) / bd, M.nlev + 1), bd, 0, s>>>(M, lam_u + nh, u + nh, grad_beta_up,
+                                                                              grad_beta_dn);
+    CK(cudaGetLastError());
+    return MG_OK;
 }
 
 mg_status mixed_apply_transpose(mg_handle* h, const double* u, const double* p, double* yu, double* yp,

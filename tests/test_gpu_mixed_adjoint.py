@@ -149,3 +149,34 @@ def test_autograd_gradient_and_central_differences(mg, name):
         fd = (L(eps * du, eps * dp) - L(-eps * du, -eps * dp)) / (2 * eps)
         assert abs(fd - grad @ d) <= 1e-6 * abs(grad @ d) + 1e-9 * np.linalg.norm(grad) * np.linalg.norm(d)
     h.destroy()
+
+
+@pytest.mark.parametrize("name", ["m4l6", "m2l4f4", "m4l6f4"])
+def test_coefficient_gradient(mg, name):
+    """mixed_coefficient_gradient against oracle.reference.mixed_coefficient_gradient: on the
+    oracle's own solution and adjoint (the kernel's arithmetic, to rounding), and end to end
+    from the GPU's forward and adjoint solves (to the solves' accuracy)."""
+    from oracle.reference import adjoint_solve, direct_solve, mixed_coefficient_gradient
+    cfg, inp, S, A = problem(name)
+    h = mg.mg_setup_config(cfg, inp, precision="fp32")
+    rhs = np.concatenate([inp["rhs_u"], inp["rhs_p"]])
+    w = syn.normal(83, 0, S.nu + S.np)
+    x = direct_solve(A, rhs)
+    lam = adjoint_solve(A, w)
+    ref = mixed_coefficient_gradient(S, x, lam, cfg.eps)
+    nv = (S.nlev + 1) * S.ncol
+    gg, gu, gd = _zeros(S.np), _zeros(nv), _zeros(nv)
+    mg.mixed_coefficient_gradient(h, dev(lam[:S.nu]), dev(x[:S.nu]), dev(x[S.nu:]), gg, gu, gd)
+    for got, r in zip((gg, gu, gd), ref):
+        r = r.ravel()
+        assert np.allclose(host(got), r, rtol=1e-12, atol=1e-13 * np.abs(r).max())
+    # end to end: GPU solution and adjoint
+    u, p = _zeros(S.nu), _zeros(S.np)
+    assert mg.mixed_solve(h, dev(inp["rhs_u"]), dev(inp["rhs_p"]), u, p, tol=1e-12).converged
+    lu, lp = _zeros(S.nu), _zeros(S.np)
+    assert mg.mixed_solve_adjoint(h, dev(w[:S.nu]), dev(w[S.nu:]), lu, lp, tol=1e-12).converged
+    mg.mixed_coefficient_gradient(h, lu, u, p, gg, gu, gd)
+    for got, r in zip((gg, gu, gd), ref):
+        r = r.ravel()
+        assert np.linalg.norm(host(got) - r) <= 1e-8 * np.linalg.norm(r)
+    h.destroy()

@@ -68,3 +68,45 @@ def test_transposed_mixed_operator_is_similar_to_the_transposed_mass_system(cons
     assert np.allclose(Ahat[:nu, :nu], (M.T * W[None, :]) / W[:, None], rtol=1e-12, atol=1e-15)
     if consistent or rotation:
         assert not np.allclose(Ahat[:nu, :nu], M)              # the mass is not W-symmetric
+
+
+def test_mixed_coefficient_gradient_matches_central_differences():
+    """dL/dg and dL/dbeta of L = <w, A(g, beta)^-1 rhs> from
+    oracle.reference.mixed_coefficient_gradient against central differences of single
+    background factors (interior and top cells) and single mass couplings."""
+    from oracle.reference import mixed_coefficient_gradient
+    cfg = syn.small_config(2, 5, levels=1, seed=syn.BASE_SEED + 81, mixed=True,
+                           consistent_mass=True, rotation=5e-4)
+    inp = syn.make_inputs(cfg)
+    rhs = np.concatenate([inp["rhs_u"], inp["rhs_p"]])
+    S, _ = mixed_problem(cfg, inp)
+    w = syn.normal(82, 0, S.nu + S.np)
+    A = assemble_mixed(S)
+    x = direct_solve(A, rhs)
+    dg, dbu, dbd = mixed_coefficient_gradient(S, x, adjoint_solve(A, w), cfg.eps)
+
+    def loss(**kw):
+        i2 = dict(inp, **kw)
+        S2, _ = mixed_problem(cfg, i2)
+        return w @ direct_solve(assemble_mixed(S2), rhs)
+
+    ncol = S.ncol
+    g = inp["g"].reshape(cfg.nlev, ncol)
+    for (k, c) in [(0, 3), (2, 10), (cfg.nlev - 1, 17)]:
+        h = 1e-5 * g[k, c]
+        gp, gm = g.copy(), g.copy()
+        gp[k, c] += h
+        gm[k, c] -= h
+        fd = (loss(g=gp.ravel()) - loss(g=gm.ravel())) / (2 * h)
+        assert abs(fd - dg[k, c]) <= 1e-6 * abs(dg[k, c]) + 1e-12, (k, c, fd, dg[k, c])
+    for name, arr, grad, kf in [("beta_up", inp["beta_up"], dbu, 2), ("beta_dn", inp["beta_dn"], dbd, 3)]:
+        b = arr.reshape(cfg.nlev + 1, ncol)
+        c = 5
+        h = 1e-4
+        bp, bm = b.copy(), b.copy()
+        bp[kf, c] += h
+        bm[kf, c] -= h
+        fd = (loss(**{name: bp.ravel()}) - loss(**{name: bm.ravel()})) / (2 * h)
+        assert abs(fd - grad[kf, c]) <= 1e-6 * abs(grad[kf, c]) + 1e-12, (name, fd, grad[kf, c])
+    # couplings that do not exist carry no gradient
+    assert np.all(dbu[0] == 0) and np.all(dbu[cfg.nlev - 1:] == 0) and np.all(dbd[:2] == 0)
