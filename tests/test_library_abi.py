@@ -100,6 +100,10 @@ def test_null_handle_calls_are_rejected(lib):
     assert lib.vcycle(None, vp(8), vp(16), None) == -1
     assert lib.pressure_solve(None, vp(8), vp(16), 1e-8, None, None) == -1
     assert lib.mixed_solve(None, vp(8), vp(16), vp(24), vp(32), 1e-8, None, None) == -1
+    assert lib.mixed_solve_adjoint(None, vp(8), vp(16), vp(24), vp(32), 1e-8, None, None) == -1
+    assert lib.mixed_apply_transpose(None, vp(8), vp(16), vp(24), vp(32), None) == -1
+    assert lib.mixed_coefficient_gradient(None, vp(8), vp(16), vp(24), vp(32), vp(40), vp(48), None) == -1
+    assert lib.pressure_solve_adjoint(None, vp(8), vp(16), 1e-8, None, None) == -1
     assert lib.mg_sizes(None, None, None, None) == -1
     assert lib.ensemble_pressure_solve(None, 0, None, None, 1e-8, None, None, None) == 0    # nothing to do
     assert lib.ensemble_pressure_solve(None, 1, None, None, 1e-8, None, None, None) == -1
