@@ -332,6 +332,18 @@ def run_ensemble(args, mg, torch, world, rank):
         mg.ensemble_pressure_solve(hs, bs, xs, tol=args.tol)
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    # the ensemble with the built-in launch shapes, then every member autotuned (untimed)
+    e0.record()
+    for _ in range(args.steps):
+        mg.ensemble_pressure_solve(hs, bs, xs, tol=args.tol)
+    e1.record()
+    torch.cuda.synchronize()
+    untuned_ms = e0.elapsed_time(e1) / args.steps
+    tuned = [mg.mg_autotune(h) for h in hs]
+    for h, b, x in zip(hs, bs, xs):
+        mg.pressure_solve(h, b, x, tol=args.tol)   # recapture the per-iteration graphs
+    mg.ensemble_pressure_solve(hs, bs, xs, tol=args.tol)
+    torch.cuda.synchronize()
     with Clocks(0) as clk:
         e0.record()
         for _ in range(args.steps):
@@ -359,6 +371,10 @@ def run_ensemble(args, mg, torch, world, rank):
                                f"V-cycle, GCR(5), tol {args.tol:g}", "cells": cells, "members": len(hs)},
         "sequential": {"members_per_s": round(len(hs) / (seq_ms * 1e-3), 2), "ms": round(seq_ms, 3)},
         "speedup_vs_sequential": round(seq_ms / ens_ms, 3),
+        "autotune": {"note": "value and sequential use the launch shapes mg_autotune chose per member and level",
+                     "untuned_ensemble_ms": round(untuned_ms, 3),
+                     "speedup_vs_untuned": round(untuned_ms / ens_ms, 3),
+                     "finest_level_choices": sorted({tuple(t[0]) for t in tuned})},
         "member_latency_ms": {"p50": round(float(np.percentile(lat, 50)), 3),
                               "p99": round(float(np.percentile(lat, 99)), 3), "max": round(float(lat[-1]), 3)},
         "clocks": clk.result,

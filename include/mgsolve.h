@@ -274,6 +274,21 @@ mg_status mixed_solve_adjoint(mg_handle* h, const double* g_u, const double* g_p
 mg_status mixed_coefficient_gradient(mg_handle* h, const double* lam_u, const double* u, const double* p,
                                      double* grad_g, double* grad_beta_up, double* grad_beta_dn, void* stream);
 
+/* Autotuner of the column tiles: for every multigrid level, times the candidate launch
+ * shapes of the block-Jacobi sweep (64 or 128 threads per block: 32 or 64 columns) and of
+ * the residual + restriction (4, 8, 16, 24, 35 or 70 levels per thread; on FP32 levels whose
+ * n is a multiple of 16 also the copy-ring or register-ring kernel) with CUDA events around
+ * every launch of full V-cycles on the handle's own buffers, and keeps the fastest shape per
+ * level for every later call.  Every shape gives the same result bit for bit (each output
+ * element is computed by one thread from the same inputs in the same order), so tuning
+ * changes times only.  Synchronous; a few dozen V-cycles; drops the handle's cached GCR
+ * graphs (they are captured again by the next solve).  MG_ERR_UNSUPPORTED while per-launch
+ * profiling (mg_profile_start) is on.
+ * choices: NULL or 3 * levels int32 written per level: sweep threads per block, restriction
+ * levels per thread, 1 copy ring / 0 register ring (0 and -1 on the coarsest level, which has
+ * no restriction). */
+mg_status mg_autotune(mg_handle* h, int32_t* choices, void* stream);
+
 /* [u; p] = P_mixed [ru; rp], the Schur-complement preconditioner with one V-cycle. */
 mg_status schur_precond(mg_handle* h, const double* ru, const double* rp, double* u, double* p,
                         void* stream);

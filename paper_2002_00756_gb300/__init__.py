@@ -85,6 +85,7 @@ _SIGS = {
     "mixed_apply_transpose": [_VP, _DP, _DP, _DP, _DP, _VP],
     "mixed_solve_adjoint": [_VP, _DP, _DP, _DP, _DP, _D, ctypes.POINTER(_Info), _VP],
     "mixed_coefficient_gradient": [_VP, _DP, _DP, _DP, _DP, _DP, _DP, _VP],
+    "mg_autotune": [_VP, ctypes.POINTER(ctypes.c_int32), _VP],
     "schur_precond": [_VP, _DP, _DP, _DP, _DP, _VP],
     "mg_profile_start": [_VP, _I32, _I32, _I32],
     "mg_profile_stop": [_VP, ctypes.POINTER(_KRec), _I32, ctypes.POINTER(ctypes.c_int32)],
@@ -355,6 +356,15 @@ def mixed_coefficient_gradient(h: Handle, lam_u, u, p, grad_g, grad_beta_up, gra
                                              _ptr(grad_beta_up, nv, "grad_beta_up"),
                                              _ptr(grad_beta_dn, nv, "grad_beta_dn"), _stream(stream)),
            "mixed_coefficient_gradient")
+
+
+def mg_autotune(h: Handle, stream=None) -> list[tuple[int, int, int]]:
+    """Pick the fastest sweep and restriction launch shapes per level (see mg_autotune in
+    mgsolve.h); returns (sweep threads per block, restriction levels per thread, copy ring)
+    per level."""
+    ch = (ctypes.c_int32 * (3 * h.levels))()
+    _check(load().mg_autotune(h.ptr, ch, _stream(stream)), "mg_autotune")
+    return [(ch[3 * l], ch[3 * l + 1], ch[3 * l + 2]) for l in range(h.levels)]
 
 
 def mixed_apply_transpose(h: Handle, u, p, yu, yp, stream=None):

@@ -4,6 +4,7 @@
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -87,6 +88,10 @@ struct DevLevel {
     float* x32[2] = {nullptr, nullptr};
     float* b32 = nullptr;
     float* r32 = nullptr;
+    // launch shapes chosen by mg_autotune (0 / -1: the built-in choice)
+    int sweep_bd = 0;          // threads per sweep block, a multiple of 64
+    int restrict_kc = 0;       // levels per thread of the residual + restriction
+    int restrict_async = -1;   // 1: copy-ring restriction (FP32 levels, n % 16 = 0), 0: register ring
 };
 
 }  // namespace
@@ -307,7 +312,7 @@ mg_status launch_sweep(mg_handle* h, int lev, const Lvl<T, C>& L, const X* x, co
         DEEP * (sizeof(B) + sizeof(T) + (sizeof(C) >= 4 ? 3 * sizeof(C) : (MG_SWEEP_BF16_PAIRS ? 12 : 0))) +
         2 * (size_t)hsteps * sizeof(T);
     const size_t per_block = (size_t)L.nlev * sizeof(T);   // the 1/dz table
-    int bd = sweep_block(2 * L.ncol);
+    int bd = h->lv[lev].sweep_bd > 0 ? h->lv[lev].sweep_bd : sweep_block(2 * L.ncol);
 #if MG_SWEEP_WARP_HALVES
     constexpr int BQ = 64;   // the halves of a column lie in different warps
 #else
@@ -344,14 +349,17 @@ mg_status launch_restrict(mg_handle* h, int lev, const Lvl<T, C>& L, const X* x,
         const int warps = 6 * (L.n / 2) * (L.n / 16);
         // levels per thread: on a level large enough to fill the GPU several times over, long
         // chunks (fewer prologues); smaller levels need the threads of short chunks
-        const int kc = L.ncol >= MG_RESTRICT_BIG_NCOL ? MG_RESTRICT_KCHUNK_BIG : MG_RESTRICT_KCHUNK;
+        const int kc = h->lv[lev].restrict_kc > 0 ? h->lv[lev].restrict_kc
+                       : L.ncol >= MG_RESTRICT_BIG_NCOL ? MG_RESTRICT_KCHUNK_BIG
+                                                        : MG_RESTRICT_KCHUNK;
         const dim3 grid((warps + 3) / 4, (L.nlev + kc - 1) / kc);
         constexpr bool ASYNC = MG_RESTRICT_ASYNC && !XZERO && std::is_same<T, float>::value &&
                                std::is_same<C, float>::value && std::is_same<X, float>::value &&
                                std::is_same<B, float>::value && std::is_same<O, float>::value;
         bool async_done = false;
         if constexpr (ASYNC) {
-            if (L.ncol >= MG_RESTRICT_ASYNC_NCOL) {
+            const int ra = h->lv[lev].restrict_async;
+            if (ra >= 0 ? ra == 1 : L.ncol >= MG_RESTRICT_ASYNC_NCOL) {
                 mg::k_resid_restrict16a<MG_RESTRICT_DEEP, MG_RESTRICT_ASHAL><<<grid, 128, 0, s>>>(L, x, b, w, bc,
                                                                                                  ncol_c, kc);
                 async_done = true;
@@ -366,7 +374,9 @@ mg_status launch_restrict(mg_handle* h, int lev, const Lvl<T, C>& L, const X* x,
     const int bd = ncol_c >= 128 * 300 ? 128 : (ncol_c >= 64 * 300 ? 64 : 32);
     // chunk of levels per thread: enough threads to fill the GPU, few re-loads of the
     // 32 connectivity entries of the 4 children
-    const int kc = ncol_c >= 128 * 300 ? 3 * APPLY_KCHUNK : APPLY_KCHUNK;
+    const int kc = h->lv[lev].restrict_kc > 0 ? h->lv[lev].restrict_kc
+                   : ncol_c >= 128 * 300 ? 3 * APPLY_KCHUNK
+                                         : APPLY_KCHUNK;
     const dim3 grid((ncol_c + bd - 1) / bd, (L.nlev + kc - 1) / kc);
     mg::k_resid_restrict<T, C, XZERO, X, B, O><<<grid, bd, 0, s>>>(L, x, b, w, bc, ncol_c, kc);
     CK(cudaGetLastError());
@@ -1376,6 +1386,87 @@ mg_status schur_precond(mg_handle* h, const double* ru, const double* rp, double
     if (!h->mixed) return MG_ERR_UNSUPPORTED;
     DeviceGuard dg(h->device);
     return schur_impl(h, ru, rp, u, p, S(stream));
+}
+
+mg_status mg_autotune(mg_handle* h, int32_t* choices, void* stream) {
+    if (!h) return MG_ERR_ARG;
+    if (h->prof) return MG_ERR_UNSUPPORTED;   // the tuner uses the per-launch profiler itself
+    DeviceGuard dg(h->device);
+    cudaStream_t s = S(stream);
+    const int L = h->L;
+    const size_t N = cells(h, 0);
+    constexpr int REPS = 3;
+    // every launch of REPS V-cycles is recorded: 2 kinds x L levels x (sweeps + 1) at most
+    const int cap = 2 * REPS * L * (h->prm.n_pre + h->prm.n_post + h->prm.n_coarse + 4);
+    while ((int)h->evpool.size() < 2 * cap) {
+        cudaEvent_t e;
+        CK(cudaEventCreate(&e));
+        h->evpool.push_back(e);
+    }
+    // a V-cycle on the handle's own buffers: b = 0 (the launches, and so their times, do not
+    // depend on the values)
+    CK(cudaMemsetAsync(h->r, 0, N * sizeof(double), s));
+    std::vector<double> sweep_ms(L), restr_ms(L);
+    auto measure = [&]() -> mg_status {
+        TRY(run_vcycle(h, h->r, h->adj, s));   // warm-up with this shape
+        h->prof_kind = -1;
+        h->prof_level = -1;
+        h->recs.clear();
+        h->prof = true;
+        mg_status st = MG_OK;
+        for (int i = 0; i < REPS && st == MG_OK; ++i) st = run_vcycle(h, h->r, h->adj, s);
+        h->prof = false;
+        TRY(st);
+        CK(cudaStreamSynchronize(s));
+        std::fill(sweep_ms.begin(), sweep_ms.end(), 0.0);
+        std::fill(restr_ms.begin(), restr_ms.end(), 0.0);
+        for (size_t i = 0; i < h->recs.size(); ++i) {
+            float ms = 0.f;
+            CK(cudaEventElapsedTime(&ms, h->evpool[2 * i], h->evpool[2 * i + 1]));
+            const auto& r = h->recs[i];
+            if (r.level < 0 || r.level >= L) continue;
+            if (r.kind == MG_K_SWEEP) sweep_ms[r.level] += ms;
+            if (r.kind == MG_K_RESTRICT) restr_ms[r.level] += ms;
+        }
+        h->recs.clear();
+        return MG_OK;
+    };
+    // sweep blocks: 64 or 128 threads (two warps hold the two halves of 32 columns; the
+    // kernel's launch bounds allow 128)
+    std::vector<int> best_bd(L, 0);
+    std::vector<double> best_t(L, 1e300);
+    for (int bd : {64, 128}) {
+        for (int l = 0; l < L; ++l) h->lv[l].sweep_bd = bd;
+        TRY(measure());
+        for (int l = 0; l < L; ++l)
+            if (sweep_ms[l] < best_t[l]) best_t[l] = sweep_ms[l], best_bd[l] = bd;
+    }
+    for (int l = 0; l < L; ++l) h->lv[l].sweep_bd = best_bd[l];
+    // residual + restriction: levels per thread, copy ring or register ring
+    std::vector<int> best_kc(L, 0), best_as(L, -1);
+    std::fill(best_t.begin(), best_t.end(), 1e300);
+    for (int as : {0, 1})
+        for (int kc : {4, 8, 16, 24, 35, 70}) {
+            for (int l = 0; l < L; ++l) h->lv[l].restrict_kc = kc, h->lv[l].restrict_async = as;
+            TRY(measure());
+            for (int l = 0; l + 1 < L; ++l)
+                if (restr_ms[l] < best_t[l]) best_t[l] = restr_ms[l], best_kc[l] = kc, best_as[l] = as;
+        }
+    for (int l = 0; l < L; ++l) h->lv[l].restrict_kc = best_kc[l], h->lv[l].restrict_async = best_as[l];
+    // the cached GCR graphs hold the old launch shapes
+    for (auto& row : h->gexec)
+        for (cudaGraphExec_t& g : row)
+            if (g) {
+                cudaGraphExecDestroy(g);
+                g = nullptr;
+            }
+    if (choices)
+        for (int l = 0; l < L; ++l) {
+            choices[3 * l] = best_bd[l];
+            choices[3 * l + 1] = best_kc[l];
+            choices[3 * l + 2] = best_as[l];
+        }
+    return MG_OK;
 }
 
 mg_status mg_profile_start(mg_handle* h, int32_t capacity, int32_t kind, int32_t level) {
