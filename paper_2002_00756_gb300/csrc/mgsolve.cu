@@ -312,7 +312,8 @@ mg_status launch_sweep(mg_handle* h, int lev, const Lvl<T, C>& L, const X* x, co
         DEEP * (sizeof(B) + sizeof(T) + (sizeof(C) >= 4 ? 3 * sizeof(C) : (MG_SWEEP_BF16_PAIRS ? 12 : 0))) +
         2 * (size_t)hsteps * sizeof(T);
     const size_t per_block = (size_t)L.nlev * sizeof(T);   // the 1/dz table
-    int bd = h->lv[lev].sweep_bd > 0 ? h->lv[lev].sweep_bd : sweep_block(2 * L.ncol);
+    // (h is NULL for the allocation-free smoothing: built-in shapes)
+    int bd = (h && h->lv[lev].sweep_bd > 0) ? h->lv[lev].sweep_bd : sweep_block(2 * L.ncol);
 #if MG_SWEEP_WARP_HALVES
     constexpr int BQ = 64;   // the halves of a column lie in different warps
 #else
@@ -349,7 +350,7 @@ mg_status launch_restrict(mg_handle* h, int lev, const Lvl<T, C>& L, const X* x,
         const int warps = 6 * (L.n / 2) * (L.n / 16);
         // levels per thread: on a level large enough to fill the GPU several times over, long
         // chunks (fewer prologues); smaller levels need the threads of short chunks
-        const int kc = h->lv[lev].restrict_kc > 0 ? h->lv[lev].restrict_kc
+        const int kc = (h && h->lv[lev].restrict_kc > 0) ? h->lv[lev].restrict_kc
                        : L.ncol >= MG_RESTRICT_BIG_NCOL ? MG_RESTRICT_KCHUNK_BIG
                                                         : MG_RESTRICT_KCHUNK;
         const dim3 grid((warps + 3) / 4, (L.nlev + kc - 1) / kc);
@@ -358,7 +359,7 @@ mg_status launch_restrict(mg_handle* h, int lev, const Lvl<T, C>& L, const X* x,
                                std::is_same<B, float>::value && std::is_same<O, float>::value;
         bool async_done = false;
         if constexpr (ASYNC) {
-            const int ra = h->lv[lev].restrict_async;
+            const int ra = h ? h->lv[lev].restrict_async : -1;
             if (ra >= 0 ? ra == 1 : L.ncol >= MG_RESTRICT_ASYNC_NCOL) {
                 mg::k_resid_restrict16a<MG_RESTRICT_DEEP, MG_RESTRICT_ASHAL><<<grid, 128, 0, s>>>(L, x, b, w, bc,
                                                                                                  ncol_c, kc);
@@ -374,7 +375,7 @@ mg_status launch_restrict(mg_handle* h, int lev, const Lvl<T, C>& L, const X* x,
     const int bd = ncol_c >= 128 * 300 ? 128 : (ncol_c >= 64 * 300 ? 64 : 32);
     // chunk of levels per thread: enough threads to fill the GPU, few re-loads of the
     // 32 connectivity entries of the 4 children
-    const int kc = h->lv[lev].restrict_kc > 0 ? h->lv[lev].restrict_kc
+    const int kc = (h && h->lv[lev].restrict_kc > 0) ? h->lv[lev].restrict_kc
                    : ncol_c >= 128 * 300 ? 3 * APPLY_KCHUNK
                                          : APPLY_KCHUNK;
     const dim3 grid((ncol_c + bd - 1) / bd, (L.nlev + kc - 1) / kc);
