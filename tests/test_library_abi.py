@@ -110,3 +110,43 @@ def test_null_handle_calls_are_rejected(lib):
     hs = (ctypes.c_void_p * 1)(None)
     assert lib.ensemble_pressure_solve(hs, 1, hs, hs, 1e-8, None, None, None) == -1     # NULL member
     lib.mg_destroy(None)
+
+
+def test_binding_rejects_host_and_mistyped_vectors(lib):
+    """Every vector argument of the binding must be a contiguous float64 CUDA tensor of the
+    handle's size; the check runs before the library is called (no GPU needed to see it)."""
+    torch = pytest.importorskip("torch")
+    import paper_2002_00756_gb300 as mg
+    n, nlev = 2, 3
+    ncol = 6 * n * n
+    # a placeholder pointer: every vector is checked before the library is called, so it is
+    # never passed on (and is cleared below before the handle's destructor could use it)
+    h = mg.Handle(8, n, nlev, 1, ncol, ncol * nlev, 2 * ncol * nlev + ncol * (nlev + 1))
+    c = torch.zeros(h.ncell, dtype=torch.float64)            # host tensor
+    u = torch.zeros(h.nu, dtype=torch.float64)
+    v = torch.zeros((nlev + 1) * ncol, dtype=torch.float64)
+    calls = [
+        lambda: mg.helmholtz_apply(h, c, c),
+        lambda: mg.vcycle(h, c, c),
+        lambda: mg.pressure_solve(h, c, c),
+        lambda: mg.pressure_solve_adjoint(h, c, c),
+        lambda: mg.helmholtz_coefficient_gradient(h, c, c, torch.zeros(6 * h.ncell, dtype=torch.float64)),
+        lambda: mg.mixed_solve(h, u, c, u, c),
+        lambda: mg.mixed_solve_adjoint(h, u, c, u, c),
+        lambda: mg.mixed_apply(h, u, c, u, c),
+        lambda: mg.mixed_apply_transpose(h, u, c, u, c),
+        lambda: mg.schur_precond(h, u, c, u, c),
+        lambda: mg.mixed_coefficient_gradient(h, u, u, c, c, v, v),
+        lambda: mg.mg_smooth(h, 0, c, c, c, 1),
+        lambda: mg.mg_smooth_noalloc(h, 0, c, c, c, 1),
+    ]
+    try:
+        for call in calls:
+            with pytest.raises(TypeError, match="contiguous float64 CUDA tensor"):
+                call()
+    finally:
+        h._ptr = ctypes.c_void_p(None)
+    with pytest.raises(TypeError):
+        mg._ptr(torch.zeros(4, dtype=torch.float32), 4)
+    with pytest.raises(ValueError, match="expected 4"):
+        mg._host(np.zeros(5), 4, "x")
