@@ -64,6 +64,22 @@ class Level:
             self.a_up[k] = flux / mesh.dz[k]
             self.a_dn[k + 1] = flux / mesh.dz[k + 1]
 
+    @classmethod
+    def from_couplings(cls, mesh: Mesh, a_h: np.ndarray, a_up: np.ndarray, a_dn: np.ndarray) -> "Level":
+        """A level whose couplings are given directly (the operator supplied by a caller
+        instead of being discretised from background factors): a_h (4, nlev, ncol) towards
+        E, W, N, S, a_up / a_dn (nlev, ncol), zero above the top / below the bottom cell."""
+        lev = cls.__new__(cls)
+        lev.mesh = mesh
+        lev.a_h = np.array(a_h, dtype=np.float64).reshape(4, mesh.nlev, mesh.ncol)
+        lev.a_up = np.array(a_up, dtype=np.float64).reshape(mesh.nlev, mesh.ncol)
+        lev.a_dn = np.array(a_dn, dtype=np.float64).reshape(mesh.nlev, mesh.ncol)
+        return lev
+
+    def couplings(self) -> np.ndarray:
+        """The six couplings per cell as one (6, nlev, ncol) array: E, W, N, S, up, down."""
+        return np.concatenate([self.a_h, self.a_up[None], self.a_dn[None]])
+
     @property
     def shape(self):
         return (self.mesh.nlev, self.mesh.ncol)
@@ -106,6 +122,49 @@ class Level:
         for _ in range(sweeps):
             x = x + omega * self.hz_solve(self.residual(b, x))
         return x
+
+
+class Level9(Level):
+    """The 9-cell stencil of Sec. 3.5 (Fig. 2): besides its four horizontal neighbours and the
+    cells directly above and below, every cell couples to the cells two levels above and two
+    below, so the column blocks H_z are pentadiagonal.  The smoother keeps only the
+    tridiagonal part H_z-hat (Sec. 3.6: the next-to-nearest couplings are dropped from the
+    column solve, while the residual b - H x keeps them).
+
+    At lowest order the paper's operator has no such couplings; here they are a flux between
+    cells k and k + 2 of the same form as the nearest one,
+        b_up[k] = gamma2 (c_s dt)^2 g_(k,k+2) / (dz_k (z_c[k+2] - z_c[k])),
+        b_dn[k + 2] = the same flux / dz_(k+2),   g_(k,k+2) = (g_k + g_(k+2)) / 2,
+    with a relative strength gamma2, so V H stays symmetric and H an M-matrix.  H_z-hat drops
+    these fluxes entirely (the off-diagonal entries and their share of the diagonal): keeping
+    the share on the diagonal would make H_z-hat differ from H by 2 b on the vertically smooth
+    error, which the column solve then fails to reduce."""
+
+    def __init__(self, mesh: Mesh, g: np.ndarray, cs_dt: float, gamma2: float, mu=None, mu_h=None):
+        super().__init__(mesh, g, cs_dt, mu, mu_h)
+        nlev, ncol = mesh.nlev, mesh.ncol
+        self.gamma2 = float(gamma2)
+        self.b_up = np.zeros((nlev, ncol))
+        self.b_dn = np.zeros((nlev, ncol))
+        c2 = cs_dt * cs_dt
+        for k in range(nlev - 2):
+            gf = 0.5 * (self.g[k] + self.g[k + 2])
+            flux = self.gamma2 * c2 * gf / (mesh.zc[k + 2] - mesh.zc[k])
+            self.b_up[k] = flux / mesh.dz[k]
+            self.b_dn[k + 2] = flux / mesh.dz[k + 2]
+
+    def diag(self) -> np.ndarray:
+        return super().diag() + self.b_up + self.b_dn
+
+    def apply(self, x: np.ndarray) -> np.ndarray:
+        x = np.asarray(x, dtype=np.float64).reshape(self.shape)
+        y = super().apply(x)
+        y[:-2] += self.b_up[:-2] * (x[:-2] - x[2:])
+        y[2:] += self.b_dn[2:] * (x[2:] - x[:-2])
+        return y
+
+    # hz_solve is Level's: H_z-hat drops the next-to-nearest fluxes b (x_i - x_(i+-2)) as a whole,
+    # their diagonal share included, so it is the same tridiagonal matrix as without them.
 
 
 def thomas(lower: np.ndarray, diag: np.ndarray, upper: np.ndarray, r: np.ndarray) -> np.ndarray:

@@ -75,3 +75,61 @@ def gcr(A: Callable, b: np.ndarray, P: Callable | None = None, tol: float = 1e-8
         if hist[-1] <= tol:
             break
     return g.x, it, hist
+
+
+def bicgstab(A: Callable, b: np.ndarray, P: Callable | None = None, tol: float = 1e-8,
+             maxiter: int = 500):
+    """BiCGStab(A, P, eps) of the solver list of Sec. 4.1, used in Table 1 as the pressure solver
+    K_H of the "Krylov" and "Krylov-MG" configurations.  The paper does not print the
+    recurrences; this is van der Vorst's stabilised biconjugate gradient method (SIAM J. Sci.
+    Stat. Comput. 13, 1992) with the preconditioner applied on the right, x0 = 0 and the shadow
+    residual r^ = r0 = b:
+
+        rho = <r^, r>;  p = r + (rho / rho_old)(alpha / omega)(p - omega v)   (p = r first)
+        p^ = P p,  v = A p^,  alpha = rho / <r^, v>,  s = r - alpha v
+        stop with x += alpha p^ if ||s|| <= tol ||b||                          (half step)
+        s^ = P s,  t = A s^,  omega = <t, s> / <t, t>
+        x += alpha p^ + omega s^,  r = s - omega t,  stop if ||r|| <= tol ||b||
+
+    Each full step applies A and P twice (the cost 2 n_iter (C_H + C_Hz) + C_H of Sec. 3.7).
+    Returns (x, iterations with a half step counted as 0.5, history of ||r|| / ||b||)."""
+    P = (lambda v: v) if P is None else P
+    b = np.asarray(b, dtype=np.float64).ravel()
+    x = np.zeros_like(b)
+    nb = np.linalg.norm(b)
+    hist = [1.0]
+    if nb == 0.0:
+        return x, 0.0, hist
+    r = b.copy()
+    rh = b.copy()
+    p = np.zeros_like(b)
+    v = np.zeros_like(b)
+    rho_old = alpha = omega = 1.0
+    it = 0.0
+    for i in range(maxiter):
+        rho = np.dot(rh, r)
+        if rho == 0.0 or not np.isfinite(rho):
+            raise FloatingPointError("BiCGStab breakdown: <r^, r> = %r" % rho)
+        p = r.copy() if i == 0 else r + (rho / rho_old) * (alpha / omega) * (p - omega * v)
+        ph = np.asarray(P(p), dtype=np.float64).ravel()
+        v = np.asarray(A(ph), dtype=np.float64).ravel()
+        alpha = rho / np.dot(rh, v)
+        s = r - alpha * v
+        ns = np.linalg.norm(s) / nb
+        if ns <= tol:
+            x = x + alpha * ph
+            hist.append(ns)
+            return x, it + 0.5, hist
+        sh = np.asarray(P(s), dtype=np.float64).ravel()
+        t = np.asarray(A(sh), dtype=np.float64).ravel()
+        omega = np.dot(t, s) / np.dot(t, t)
+        if omega == 0.0 or not np.isfinite(omega):
+            raise FloatingPointError("BiCGStab breakdown: omega = %r" % omega)
+        x = x + alpha * ph + omega * sh
+        r = s - omega * t
+        rho_old = rho
+        it += 1.0
+        hist.append(np.linalg.norm(r) / nb)
+        if hist[-1] <= tol:
+            break
+    return x, it, hist

@@ -24,7 +24,7 @@ from __future__ import annotations
 import numpy as np
 
 from .geometry import Mesh
-from .helmholtz import Level
+from .helmholtz import Level, Level9
 
 
 def restrict_field(fine: Mesh, coarse: Mesh, f: np.ndarray) -> np.ndarray:
@@ -65,7 +65,8 @@ class Hierarchy:
     """Meshes and rediscretised operators on levels 1..L (index 0 = finest)."""
 
     def __init__(self, n: int, z_if: np.ndarray, radius: float, levels: int, g: np.ndarray,
-                 cs_dt: float, mu: np.ndarray | None = None, mu_h: np.ndarray | None = None):
+                 cs_dt: float, mu: np.ndarray | None = None, mu_h: np.ndarray | None = None,
+                 gamma2: float = 0.0):
         if n % (1 << (levels - 1)):
             raise ValueError("C_n must be divisible by 2^(L-1)")
         self.meshes = [Mesh(n >> l, z_if, radius) for l in range(levels)]
@@ -80,7 +81,17 @@ class Hierarchy:
                     mu = restrict_field(self.meshes[l - 1], m, mu)
                 if mu_h is not None:
                     mu_h = restrict_side_field(self.meshes[l - 1], m, mu_h)
-            self.levels.append(Level(m, g, cs_dt, mu, mu_h))
+            # gamma2 > 0: the 9-cell stencil (Sec. 3.5), rediscretised on every level
+            self.levels.append(Level9(m, g, cs_dt, gamma2, mu, mu_h) if gamma2 > 0.0 else Level(m, g, cs_dt, mu, mu_h))
+
+    def with_finest(self, level: Level) -> "Hierarchy":
+        """The same hierarchy with the finest operator replaced (coarse levels unchanged): the
+        hierarchy of a caller-supplied finest operator whose coarse levels are rediscretised
+        from background factors."""
+        out = Hierarchy.__new__(Hierarchy)
+        out.meshes = self.meshes
+        out.levels = [level] + self.levels[1:]
+        return out
 
     @property
     def L(self) -> int:

@@ -9,7 +9,7 @@ from .mixed import MixedSystem
 def pressure_hierarchy(cfg, inp, levels: int | None = None) -> Hierarchy:
     """Helmholtz hierarchy of the pressure-only workload (Sec. 3.5-3.6)."""
     return Hierarchy(cfg.n, inp["z_if"], cfg.radius, levels or cfg.levels, inp["g"],
-                     cfg.cs * cfg.dt)
+                     cfg.cs * cfg.dt, gamma2=cfg.gamma2)
 
 
 TAU_U = 0.5     # off-centring of the velocity equation (Sec. 3.3, tau_u = 1/2)

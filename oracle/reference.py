@@ -34,6 +34,13 @@ def assemble_helmholtz(H: Level) -> sp.csr_matrix:
     rows.append(idx[1:].ravel())
     cols.append(idx[:-1].ravel())
     vals.append(-H.a_dn[1:].ravel())
+    if hasattr(H, "b_up"):          # the 9-cell stencil: couplings two levels up and down
+        rows.append(idx[:-2].ravel())
+        cols.append(idx[2:].ravel())
+        vals.append(-H.b_up[:-2].ravel())
+        rows.append(idx[2:].ravel())
+        cols.append(idx[:-2].ravel())
+        vals.append(-H.b_dn[2:].ravel())
     return sp.csr_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))),
                          shape=(N, N))
 

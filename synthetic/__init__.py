@@ -104,6 +104,7 @@ class Config:
     eps: float = 0.05           # strength of the non-symmetric vertical coupling
     consistent_mass: bool = False   # mixed: consistent instead of lumped velocity mass
     rotation: float = 0.0       # mixed: planet angular velocity Omega [1/s] of the Coriolis term
+    gamma2: float = 0.0         # > 0: 9-cell stencil, strength of the couplings two levels apart
     cs: float = 340.0           # speed of sound, m/s
     dt: float = 600.0           # time step, s
     radius: float = 6371.0e3    # planet radius, m

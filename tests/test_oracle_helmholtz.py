@@ -181,3 +181,83 @@ def test_mu_scales_only_vertical_coefficients():
     L2 = Level(L1.mesh, L1.g, CSDT, mu)
     assert np.array_equal(L1.a_h, L2.a_h)
     assert np.allclose(L2.a_up, 0.5 * L1.a_up) and np.allclose(L2.a_dn, 0.5 * L1.a_dn)
+
+
+def test_level_from_couplings_brute_force_dense_matrix():
+    """A level given by arbitrary couplings (a caller's operator): its assembled matrix equals
+    the dense matrix built entry by entry from the definition (H x)_i = x_i + sum_f a_if (x_i - x_j),
+    and it maps constants to themselves whatever the couplings."""
+    from oracle.geometry import Mesh
+    from oracle.helmholtz import Level
+    from oracle.reference import assemble_helmholtz
+    import synthetic as syn
+    mesh = Mesh(2, syn.z_interfaces(3), 6.371e6)
+    nlev, ncol = mesh.nlev, mesh.ncol
+    rng = np.random.default_rng(5)
+    a_h = rng.uniform(0.0, 2.0, (4, nlev, ncol))
+    a_up = rng.uniform(0.0, 3.0, (nlev, ncol))
+    a_dn = rng.uniform(0.0, 3.0, (nlev, ncol))
+    a_up[-1] = 0.0
+    a_dn[0] = 0.0
+    lev = Level.from_couplings(mesh, a_h, a_up, a_dn)
+    N = nlev * ncol
+    A = np.eye(N)
+    for k in range(nlev):
+        for c in range(ncol):
+            i = k * ncol + c
+            for d in range(4):
+                j = k * ncol + mesh.nbr[d][c]
+                A[i, i] += a_h[d, k, c]
+                A[i, j] -= a_h[d, k, c]
+            if k + 1 < nlev:
+                A[i, i] += a_up[k, c]
+                A[i, i + ncol] -= a_up[k, c]
+            if k > 0:
+                A[i, i] += a_dn[k, c]
+                A[i, i - ncol] -= a_dn[k, c]
+    assert np.allclose(assemble_helmholtz(lev).toarray(), A, rtol=0, atol=1e-14)
+    assert np.allclose(lev.apply(np.full(N, 2.5)), 2.5, rtol=1e-14, atol=0)
+    assert np.array_equal(lev.couplings(), np.concatenate([a_h, a_up[None], a_dn[None]]))
+
+
+def test_nine_point_level_against_its_definition():
+    """Level9 (the 9-cell stencil of Sec. 3.5): the assembled matrix equals the dense matrix
+    built entry by entry (7-cell stencil plus fluxes to the cells two levels up and down),
+    V H is symmetric, constants map to themselves, gamma2 = 0 gives the 7-cell level, and one
+    block-Jacobi sweep is x0 + omega Hz^-1 (b - H x0) with Hz the tridiagonal column matrix
+    without the next-to-nearest fluxes."""
+    from oracle.geometry import Mesh
+    from oracle.helmholtz import Level, Level9
+    from oracle.reference import assemble_helmholtz
+    import synthetic as syn
+    mesh = Mesh(2, syn.z_interfaces(6), 6.371e6)
+    nlev, ncol = mesh.nlev, mesh.ncol
+    g = np.exp(0.1 * syn.normal(4, 1, nlev * ncol)).reshape(nlev, ncol)
+    L7 = Level(mesh, g, CSDT)
+    L9 = Level9(mesh, g, CSDT, 0.3)
+    A7 = assemble_helmholtz(L7).toarray()
+    A = A7.copy()
+    c2 = CSDT * CSDT
+    for k in range(nlev - 2):
+        for c in range(ncol):
+            flux = 0.3 * c2 * 0.5 * (g[k, c] + g[k + 2, c]) / (mesh.zc[k + 2] - mesh.zc[k])
+            i, j = k * ncol + c, (k + 2) * ncol + c
+            A[i, i] += flux / mesh.dz[k]
+            A[i, j] -= flux / mesh.dz[k]
+            A[j, j] += flux / mesh.dz[k + 2]
+            A[j, i] -= flux / mesh.dz[k + 2]
+    A9 = assemble_helmholtz(L9).toarray()
+    assert np.allclose(A9, A, rtol=1e-13, atol=0)
+    V = (mesh.area[None, :] * mesh.dz[:, None]).ravel()
+    VA = V[:, None] * A9
+    assert np.allclose(VA, VA.T, rtol=1e-12, atol=1e-12 * np.abs(VA).max())
+    assert np.allclose(L9.apply(np.full(nlev * ncol, -1.5)), -1.5, rtol=1e-13, atol=0)
+    x = syn.normal(4, 2, nlev * ncol)
+    assert np.array_equal(Level9(mesh, g, CSDT, 0.0).apply(x), L7.apply(x))
+    assert np.allclose(L9.apply(x).ravel(), A9 @ x, rtol=1e-12, atol=1e-9)
+    k_of = np.arange(nlev * ncol) // ncol
+    c_of = np.arange(nlev * ncol) % ncol
+    Hz = np.where((c_of[:, None] == c_of[None, :]) & (np.abs(k_of[:, None] - k_of[None, :]) <= 1), A7, 0.0)
+    b, x0 = syn.normal(4, 3, nlev * ncol), syn.normal(4, 5, nlev * ncol)
+    ref = x0 + 0.8 * np.linalg.solve(Hz, b - A9 @ x0)
+    assert np.allclose(L9.jacobi(b, x0, 0.8, 1).ravel(), ref, rtol=1e-10, atol=1e-12)

@@ -122,3 +122,48 @@ def test_coefficient_gradient_matches_central_differences():
         arr[idx] = a0
         fd = (lp - lm) / (2 * h)
         assert abs(fd - G[gi]) <= 1e-6 * abs(G[gi]) + 1e-12, (gi, fd, G[gi])
+
+
+def test_bicgstab_iterates_match_the_library_routine():
+    """BiCGStab with a right preconditioner is the algorithm scipy implements (Templates form):
+    after the same number of steps, with the same preconditioner, the iterates agree."""
+    import scipy.sparse.linalg as spla
+    from oracle.krylov import bicgstab
+    A, b = _nonsym(50, 3)
+    Dinv = 1.0 / np.diag(A)
+    for k in (1, 2, 5):
+        x, it, _ = bicgstab(lambda v: A @ v, b, lambda r: Dinv * r, tol=0.0, maxiter=k)
+        M = spla.LinearOperator(A.shape, matvec=lambda r: Dinv * r)
+        xs, info = spla.bicgstab(A, b, rtol=0.0, atol=0.0, maxiter=k, M=M)
+        assert it == k and info == k
+        assert np.linalg.norm(x - xs) <= 1e-12 * np.linalg.norm(xs)
+
+
+def test_bicgstab_exact_preconditioner_stops_at_the_half_step():
+    from oracle.krylov import bicgstab
+    A, b = _nonsym(30, 4)
+    Ainv = np.linalg.inv(A)
+    x, it, hist = bicgstab(lambda v: A @ v, b, lambda r: Ainv @ r, tol=1e-12)
+    assert it == 0.5 and hist[-1] <= 1e-12
+    assert np.allclose(x, np.linalg.solve(A, b), rtol=1e-12, atol=0)
+
+
+@pytest.mark.parametrize("precond", ["jacobi", "mg"])
+def test_bicgstab_on_the_helmholtz_problem_matches_direct_solve(precond):
+    """Krylov(eps_H) and Krylov-MG(eps_H, L) of Table 1 on a small Helmholtz problem: the true
+    residual is below eps_H and the error below the conditioning bound."""
+    from oracle.krylov import bicgstab
+    n, nlev = 4, 6
+    g = np.exp(0.1 * syn.normal(6, 1, nlev * 6 * n * n))
+    hier = Hierarchy(n, syn.z_interfaces(nlev), R, 2, g, CSDT)
+    H = hier.levels[0]
+    b = syn.normal(6, 2, nlev * 6 * n * n)
+    P = (lambda r: H.jacobi(r, np.zeros_like(r), 1.0, 1).ravel()) if precond == "jacobi" else \
+        hier.as_preconditioner()
+    xs = direct_solve(assemble_helmholtz(H), b)
+    for eps in (1e-2, 1e-6, 1e-10):
+        x, it, hist = bicgstab(lambda v: H.apply(v).ravel(), b, P, tol=eps)
+        res = np.linalg.norm(b - H.apply(x).ravel()) / np.linalg.norm(b)
+        assert res <= eps * (1 + 1e-6) and hist[-1] <= eps
+        assert it >= 0.5
+    assert np.linalg.norm(x - xs) <= 1e-8 * np.linalg.norm(xs)

@@ -13,11 +13,11 @@ R = 6371.0e3
 CSDT = 340.0 * 600.0
 
 
-def _hier(n=4, nlev=4, levels=2, seed=11, cs_dt=CSDT):
+def _hier(n=4, nlev=4, levels=2, seed=11, cs_dt=CSDT, gamma2=0.0):
     z = syn.z_interfaces(nlev)
     ncol = 6 * n * n
     g = np.exp(0.1 * syn.normal(seed, 1, nlev * ncol)).reshape(nlev, ncol)
-    return Hierarchy(n, z, R, levels, g, cs_dt)
+    return Hierarchy(n, z, R, levels, g, cs_dt, gamma2=gamma2)
 
 
 def test_restriction_is_the_volume_adjoint_of_injection():
@@ -69,6 +69,10 @@ def _dense_vcycle_matrix(h, level, omega, n_pre, n_post, n_coarse):
     k_of = np.arange(nlev * ncol) // ncol
     c_of = np.arange(nlev * ncol) % ncol
     Hz = np.where((c_of[:, None] == c_of[None, :]) & (np.abs(k_of[:, None] - k_of[None, :]) <= 1), H, 0.0)
+    lev = h.levels[level]
+    if hasattr(lev, "b_up"):
+        # 9-cell stencil: H_z-hat drops the next-to-nearest fluxes, their diagonal share too
+        Hz -= np.diag((lev.b_up + lev.b_dn).ravel())
     B = omega * np.linalg.inv(Hz)
     I = np.eye(len(H))
     S = I - B @ H
@@ -98,9 +102,10 @@ def _dense_vcycle_matrix(h, level, omega, n_pre, n_post, n_coarse):
     return Spost @ M + Mpost
 
 
+@pytest.mark.parametrize("gamma2", [0.0, 0.25])
 @pytest.mark.parametrize("levels,n_pre,n_post", [(2, 2, 2), (3, 1, 2), (2, 0, 3)])
-def test_vcycle_equals_dense_matrix_form(levels, n_pre, n_post):
-    h = _hier(n=4, nlev=4, levels=levels)
+def test_vcycle_equals_dense_matrix_form(levels, n_pre, n_post, gamma2):
+    h = _hier(n=4, nlev=5, levels=levels, gamma2=gamma2)
     M = _dense_vcycle_matrix(h, 0, 0.8, n_pre, n_post, 3)
     b = np.random.default_rng(3).standard_normal(h.levels[0].shape)
     got = h.vcycle(b, 0.8, n_pre, n_post, 3).ravel()
@@ -144,3 +149,21 @@ def test_level_count_rule_at_large_cfl():
     rho = [_contraction(16, 8.0, levels=L) for L in (1, 2, 3, 4)]
     assert rho[0] > rho[1] > rho[2] > rho[3]
     assert rho[3] < 0.5
+
+
+def test_nine_point_vcycle_contraction_is_mesh_independent():
+    # the 9-cell stencil (Sec. 3.5) smoothed with the tridiagonal H_z-hat: the V-cycle still
+    # contracts independently of the mesh, and about as fast as on the 7-cell stencil
+    def rho(n, gamma2):
+        dx = 0.5 * math.pi * R / n
+        h = _hier(n=n, nlev=10, levels=3, cs_dt=4.0 * dx, gamma2=gamma2)
+        H = h.levels[0]
+        e = np.random.default_rng(9).standard_normal(H.shape)
+        for _ in range(8):
+            e2 = e - h.vcycle(H.apply(e))
+            r = np.linalg.norm(e2) / np.linalg.norm(e)
+            e = e2
+        return r
+    r9 = [rho(n, 0.25) for n in (8, 16, 32)]
+    assert max(r9) < 0.5 and max(r9) / min(r9) < 1.5
+    assert abs(rho(16, 0.25) - rho(16, 0.0)) < 0.05
