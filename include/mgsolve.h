@@ -142,6 +142,50 @@ typedef struct mg_handle mg_handle;
 mg_status mg_setup(const mg_mesh* mesh, const mg_params* params, const double* g,
                    const mg_mixed* mixed, mg_handle** out);
 
+/* mg_setup for a finest-level operator given by its stencil coefficients (the operator /
+ * preconditioner split of Sec. 4.1: the caller supplies the operator A_H, the library builds
+ * the preconditioner P_H around it).
+ *   coeffs        HOST, 6 N doubles a[s * N + k * ncol + c]: the couplings a_{i,f} of
+ *                 Eq. helmholtz_operator in the strong form above for the sides s = E, W, N, S,
+ *                 up, down of every finest-level cell (the layout helmholtz_coefficient_gradient
+ *                 returns).  The outer Krylov solves, helmholtz_apply and the V-cycle's finest
+ *                 level use exactly this operator.
+ *   cell_factors  HOST, N background factors g > 0: the coarse operators are rediscretised
+ *                 from their volume-weighted means as in mg_setup (Sec. 3.6, last paragraph
+ *                 before Algorithm 1), so they approximate the caller's operator only as well
+ *                 as g describes it (that affects the convergence rate, not the solution).
+ * The operator must be flux-symmetric, V_i a_{i,f} = V_j a_{j,f} for the two cells of every
+ * face (to 1e-10 relative; V the cell volumes of the mesh convention above): the V-cycle keeps
+ * one value per face, and the adjoint solves rely on V H being symmetric.  Every coupling must
+ * be finite and >= 0, and the up coupling of the top cell and the down coupling of the bottom
+ * cell must be 0 (no flux through the lid or the surface).  Otherwise MG_ERR_ARG.  The
+ * pressure system only (no mixed data).  Synchronous. */
+mg_status mg_setup_coeffs(const mg_mesh* mesh, const mg_params* params, const double* coeffs,
+                          const double* cell_factors, mg_handle** out);
+
+/* mg_setup for the 9-cell stencil of Sec. 3.5 (Fig. 2): besides the 7-cell stencil above, every
+ * cell couples to the cells two levels above and below through the flux
+ *   (H x)_i += b_up,i (x_i - x_(k+2)) + b_dn,i (x_i - x_(k-2)),
+ *   b_up(k) = T2_k / dz_k, b_dn(k + 2) = T2_k / dz_(k+2),
+ *   T2_k = gamma2 (c_s dt)^2 (g_k + g_(k+2)) / 2 / (z_c(k+2) - z_c(k)),
+ * on every multigrid level (rediscretised like the rest of H), so V H stays symmetric.  The
+ * block-Jacobi smoother solves with the tridiagonal H_z-hat that drops these fluxes (Sec. 3.6):
+ * the residual b - H x keeps them, the column solve does not.  A pressure-system handle (no
+ * mixed data, no caller coefficients); precisions MG_FP64 and MG_FP32 (MG_ERR_UNSUPPORTED for
+ * BF16 coefficients).  Every pressure-system call accepts it except helmholtz_coefficient_gradient,
+ * mg_set_coefficients, mg_autotune and mg_smooth_noalloc (MG_ERR_UNSUPPORTED).  Its kernels are
+ * plain one-thread-per-cell (per-column for the Thomas solve) versions of the 7-cell ones.
+ * gamma2 > 0 and finite, else MG_ERR_ARG.  Synchronous. */
+mg_status mg_setup_9pt(const mg_mesh* mesh, const mg_params* params, const double* g, double gamma2,
+                       mg_handle** out);
+
+/* Replace the finest-level operator of a pressure handle by new couplings (DEVICE, 6 N doubles,
+ * same layout and conditions as mg_setup_coeffs); the coarse operators stay as set up.  This is
+ * the forward step of a solve differentiated with respect to its stencil coefficients.  The
+ * couplings are checked first; on MG_ERR_ARG the handle's operator is unchanged.
+ * MG_ERR_UNSUPPORTED for a handle with mixed data.  Synchronous (ordered on `stream`). */
+mg_status mg_set_coefficients(mg_handle* h, const double* coeffs, void* stream);
+
 void mg_destroy(mg_handle* h);
 
 const char* mg_status_string(mg_status s);
@@ -293,12 +337,51 @@ mg_status mg_autotune(mg_handle* h, int32_t* choices, void* stream);
 mg_status schur_precond(mg_handle* h, const double* ru, const double* rp, double* u, double* p,
                         void* stream);
 
+/* ---- the pressure solver of the Schur-complement step (Sec. 4.1, Eq. solver_notation
+ * K_mixed(A_mixed, P_mixed(K_H(A_H, P_H, eps_H)), eps); the configurations of Table 1) ---- */
+enum {
+    MG_PS_MG = 0,               /* MG(L): PreOnly, one V-cycle P_H^(MG)(L, omega, n_pre, n_post) (default) */
+    MG_PS_JACOBI = 1,           /* line relaxation: PreOnly, P_H^(Jac)(omega, sweeps) */
+    MG_PS_BICGSTAB_JACOBI = 2,  /* Krylov(eps_H): BiCGStab(A_H, P_H^(Jac)(omega, sweeps), eps_H) */
+    MG_PS_BICGSTAB_MG = 3       /* Krylov-MG(eps_H, L): BiCGStab(A_H, P_H^(MG)(L, ...), eps_H) */
+};
+
+typedef struct {
+    int32_t kind;       /* MG_PS_* */
+    double eps;         /* eps_H, relative residual of the BiCGStab kinds (Table 1: 1e-2, 1e-3, 1e-6) */
+    double omega;       /* over-relaxation of the block-Jacobi kinds (Table 1: 0.8 and 1.0) */
+    int32_t sweeps;     /* n_Jac, block-Jacobi sweeps from zero (Table 1: 10 and 1) */
+    int32_t max_iter;   /* BiCGStab iteration limit */
+} mg_pressure_solver;
+
+/* Select the pressure solver that Step 2 of the Schur-complement preconditioner (schur_precond,
+ * mixed_solve, mixed_solve_adjoint) and helmholtz_solve use.  P_H^(Jac)(omega, n) is n
+ * block-Jacobi sweeps (Eq. jacobi) from zero on the finest level; BiCGStab is van der Vorst's
+ * method with the preconditioner on the right, x0 = 0, shadow residual b, stopping when the
+ * recursively updated residual of either half step is below eps ||b||.  BiCGStab synchronises
+ * with the host once per iteration, so mixed solves that use it launch their iterations
+ * directly (no graphs); an inner solve that reaches max_iter still serves as the
+ * preconditioner.  The first selection of a BiCGStab kind allocates its 8 vectors of N doubles.
+ * Synchronous.  MG_ERR_ARG for an unknown kind or invalid parameters. */
+mg_status mg_set_pressure_solver(mg_handle* h, const mg_pressure_solver* ps);
+
+/* x = K_H(A_H, P_H, eps_H) b, the handle's pressure solver on its own (the "pressure solve" of
+ * Table 2), from x = 0.  b, x: DEVICE, N doubles.  *iterations (may be NULL): BiCGStab
+ * iterations, a half step counting 0.5 (0 for the PreOnly kinds).  MG_ERR_NOT_CONVERGED when
+ * BiCGStab reaches max_iter (x holds its last iterate), MG_ERR_BREAKDOWN on a zero or
+ * non-finite scalar.  The BiCGStab kinds are synchronous. */
+mg_status helmholtz_solve(mg_handle* h, const double* b, double* x, double* iterations, void* stream);
+
+/* BiCGStab pressure solves run since the last call (inside mixed solves or helmholtz_solve),
+ * and their iterations (half steps counting 0.5); resets both.  Either pointer may be NULL. */
+mg_status mg_inner_stats(mg_handle* h, int64_t* solves, double* iterations);
+
 /* ---- block-Jacobi smoothing that allocates nothing ----
  * The paper has no counterpart to this call: it is a service for callers that cannot
- * allocate device memory at the point where they smooth, for instance code being
- * recorded into a CUDA graph (an allocation there would end the capture), a real-time
- * loop that must not enter the allocator, or a host framework whose memory pool owns
- * all device memory after start-up.
+ * allocate device memory at the point where they smooth, for instance a real-time loop
+ * that must not enter the allocator (its latency is unbounded), a host framework whose
+ * memory pool owns all device memory after start-up, or a process that runs under a
+ * fixed device-memory budget it must not exceed.
  *
  * It computes exactly what mg_smooth computes (same kernels, same order), but it neither
  * allocates nor touches the handle's workspace: intermediate iterates are kept in one

@@ -728,6 +728,94 @@ __global__ void k_prolong(int n, int ncol, int ncol_c, int nlev, const X* __rest
     }
 }
 
+// ---------------------------------------------------------------------------------------
+// The 9-cell stencil (Sec. 3.5, Fig. 2): H also couples every cell to the cells two levels
+// above and below, through the fluxes T2[k][c] (k <-> k+2; rows nlev-2 and nlev-1 are zero):
+// b_up(k) = T2[k] / dz_k, b_dn(k) = T2[k-2] / dz_k.  These kernels run one thread per cell or
+// per column without staging: the 9-cell stencil is the paper's comparison configuration,
+// not the headline path.
+template <typename T, typename X>
+__device__ __forceinline__ T h9_cell(const Lvl<T, T>& L, const T* __restrict__ T2, const X* __restrict__ x, int k,
+                                     int c) {
+    const size_t ncol = L.ncol, o = (size_t)k * ncol;
+    const T x0 = ldx<T>(x + o + c);
+    const T* th = L.Th + (size_t)k * 2 * ncol;
+    T h = T(0);
+#pragma unroll
+    for (int s = 0; s < 4; ++s) h += __ldg(th + __ldg(L.fof + s * ncol + c)) * (x0 - ldx<T>(x + o + __ldg(L.nbr + s * ncol + c)));
+    T v = T(0);
+    if (k + 1 < L.nlev) v += __ldg(L.Tv + o + ncol + c) * (x0 - ldx<T>(x + o + ncol + c));
+    if (k > 0) v += __ldg(L.Tv + o + c) * (x0 - ldx<T>(x + o - ncol + c));
+    if (k + 2 < L.nlev) v += __ldg(T2 + o + c) * (x0 - ldx<T>(x + o + 2 * ncol + c));
+    if (k > 1) v += __ldg(T2 + o - 2 * ncol + c) * (x0 - ldx<T>(x + o - 2 * ncol + c));
+    return x0 + (__ldg(L.rA + c) * h + __ldg(L.rdz + k) * v);
+}
+
+// y = H x (9-cell stencil), one thread per cell
+template <typename T, typename X, typename Y>
+__global__ void k_apply9(Lvl<T, T> L, const T* __restrict__ T2, const X* __restrict__ x, Y* __restrict__ y) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x, k = blockIdx.y;
+    if (c >= L.ncol || k >= L.nlev) return;
+    y[(size_t)k * L.ncol + c] = (Y)h9_cell<T, X>(L, T2, x, k, c);
+}
+
+// r = b - H x (9-cell stencil; x == NULL: r = b), one thread per cell
+template <typename T, typename B>
+__global__ void k_resid9(Lvl<T, T> L, const T* __restrict__ T2, const T* __restrict__ x, const B* __restrict__ b,
+                         T* __restrict__ r) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x, k = blockIdx.y;
+    if (c >= L.ncol || k >= L.nlev) return;
+    const size_t e = (size_t)k * L.ncol + c;
+    r[e] = x ? (T)b[e] - h9_cell<T, T>(L, T2, x, k, c) : (T)b[e];
+}
+
+// x_out = x + omega Hz^-1 r per column (x == NULL: zero iterate), Hz the tridiagonal column
+// matrix of the nearest couplings (the next-to-nearest fluxes dropped, Sec. 3.6), solved by
+// the pivot-excess Thomas recurrence; sw, se hold its y / p and a_up / p per cell
+template <typename T, typename O>
+__global__ void k_thomas9(Lvl<T, T> L, const T* __restrict__ r, const T* __restrict__ x, T* __restrict__ sw,
+                          T* __restrict__ se, O* __restrict__ xo, T omega) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= L.ncol) return;
+    const size_t ncol = L.ncol;
+    const T rA = __ldg(L.rA + c);
+    T q = T(0), p = T(1), y = T(0);
+    for (int k = 0; k < L.nlev; ++k) {
+        const size_t o = (size_t)k * ncol, e = o + c;
+        const T* thk = L.Th + (size_t)k * 2 * ncol;
+        T sh = T(0);
+#pragma unroll
+        for (int s = 0; s < 4; ++s) sh += __ldg(thk + __ldg(L.fof + s * ncol + c));
+        const T rdz = __ldg(L.rdz + k);
+        const T adn = k > 0 ? rdz * __ldg(L.Tv + e) : T(0);
+        const T aup = k + 1 < L.nlev ? rdz * __ldg(L.Tv + e + ncol) : T(0);
+        const T m = k > 0 ? adn / p : T(0);
+        q = (T(1) + rA * sh) + m * q;
+        p = q + aup;
+        y = r[e] + m * y;
+        sw[e] = y / p;
+        se[e] = aup / p;
+    }
+    T d = T(0);
+    for (int k = L.nlev - 1; k >= 0; --k) {
+        const size_t e = (size_t)k * ncol + c;
+        d = sw[e] + se[e] * d;
+        xo[e] = (O)((x ? x[e] : T(0)) + omega * d);
+    }
+}
+
+// bc[k][C] = sum_q w[q][C] r[k][child_q] (restriction of a residual already formed)
+template <typename T, typename O>
+__global__ void k_restrict_sum(int n, int ncol, int nlev, const T* __restrict__ r, const T* __restrict__ w,
+                               O* __restrict__ bc, int ncol_c) {
+    const int C = blockIdx.x * blockDim.x + threadIdx.x, k = blockIdx.y;
+    if (C >= ncol_c || k >= nlev) return;
+    T acc = T(0);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) acc += __ldg(w + (size_t)q * ncol_c + C) * r[(size_t)k * ncol + child_col_dev(n, C, q)];
+    bc[(size_t)k * ncol_c + C] = (O)acc;
+}
+
 template <typename A, typename B>
 __global__ void k_convert(size_t n, const A* __restrict__ a, B* __restrict__ b) {
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)

@@ -101,6 +101,79 @@ __global__ void k_scale_volume(int ncol, int nlev, const double* __restrict__ ar
     out[e] = multiply ? x[e] * v : x[e] / v;
 }
 
+// ---- caller-supplied couplings a[s][k][c] (s = E, W, N, S, up, down) of the finest level ----
+// Their face form: Th[k][f] = a_(owner, side)(k) area(owner) (horizontal), Tv[kf][c] =
+// a_up(kf-1, c) dz[kf-1] (vertical).  Valid only for a flux-symmetric operator, V_i a_if = V_j a_jf:
+// the other cell's product must agree to 1e-10 relative, every coupling must be finite and
+// >= 0, and none may cross the surface or the lid.  A failed check sets *bad; with write the
+// kernels store the face form in every precision the handle holds (NULL arrays are skipped).
+struct CoefTargets {
+    double* Th64;
+    float* Th32;
+    __nv_bfloat16* Th16;
+    double* Tv64;
+    float* Tv32;
+    __nv_bfloat16* Tv16;
+};
+
+__device__ __forceinline__ bool coef_close(double u, double v) {
+    return fabs(u - v) <= 1e-10 * fmax(fabs(u), fabs(v));
+}
+
+__global__ void k_coef_faces(int ncol, int nlev, const int32_t* __restrict__ faceL, const int32_t* __restrict__ faceR,
+                             const int32_t* __restrict__ faceSide, const int32_t* __restrict__ nbrSide,
+                             const double* __restrict__ area, const double* __restrict__ a, bool write, CoefTargets t,
+                             unsigned int* bad) {
+    const int f = blockIdx.x * blockDim.x + threadIdx.x, k = blockIdx.y, nf = 2 * ncol;
+    if (f >= nf || k >= nlev) return;
+    const size_t N = (size_t)nlev * ncol, o = (size_t)k * ncol;
+    const int L = faceL[f], R = faceR[f], s = faceSide[f], sr = nbrSide[s * ncol + L];
+    const double tl = a[s * N + o + L] * area[L], tr = a[sr * N + o + R] * area[R];
+    if (!(tl >= 0.0) || !(tr >= 0.0) || !isfinite(tl) || !isfinite(tr) || !coef_close(tl, tr)) atomicOr(bad, 1u);
+    if (!write) return;
+    const size_t e = (size_t)k * nf + f;
+    if (t.Th64) t.Th64[e] = tl;
+    if (t.Th32) t.Th32[e] = (float)tl;
+    if (t.Th16) t.Th16[e] = __float2bfloat16_rn((float)tl);
+}
+
+__global__ void k_coef_vertical(int ncol, int nlev, const double* __restrict__ dz, const double* __restrict__ a,
+                                bool write, CoefTargets t, unsigned int* bad) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x, kf = blockIdx.y;
+    if (c >= ncol || kf > nlev) return;
+    const size_t N = (size_t)nlev * ncol;
+    double tv = 0.0;
+    if (kf == 0) {
+        if (a[5 * N + c] != 0.0) atomicOr(bad, 1u);                             // a_dn of the bottom cell
+    } else if (kf == nlev) {
+        if (a[4 * N + (size_t)(nlev - 1) * ncol + c] != 0.0) atomicOr(bad, 1u);  // a_up of the top cell
+    } else {
+        const double up = a[4 * N + (size_t)(kf - 1) * ncol + c], dn = a[5 * N + (size_t)kf * ncol + c];
+        tv = up * dz[kf - 1];
+        const double ta = dn * dz[kf];
+        if (!(up >= 0.0) || !(dn >= 0.0) || !isfinite(tv) || !isfinite(ta) || !coef_close(tv, ta)) atomicOr(bad, 1u);
+    }
+    if (!write) return;
+    const size_t e = (size_t)kf * ncol + c;
+    if (t.Tv64) t.Tv64[e] = tv;
+    if (t.Tv32) t.Tv32[e] = (float)tv;
+    if (t.Tv16) t.Tv16[e] = __float2bfloat16_rn((float)tv);
+}
+
+// a6[s][e] = a[s][e] (s < 6) and a6[6][e] = 1 + their sum: the FP64 operator of the GCR apply
+__global__ void k_coef_cells(size_t N, const double* __restrict__ a, double* __restrict__ a6) {
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < N; e += (size_t)gridDim.x * blockDim.x) {
+        double d = 1.0;
+#pragma unroll
+        for (int s = 0; s < 6; ++s) {
+            const double v = a[s * N + e];
+            a6[s * N + e] = v;
+            d += v;
+        }
+        a6[6 * N + e] = d;
+    }
+}
+
 // grad[s][e] = -lam_e (x_e - x_(neighbour s of e)), s = E, W, N, S, up, down (0 without a
 // neighbour): the gradient of L(x) with respect to the six couplings of the finest level
 __global__ void k_coef_grad(Lvl<double, double> L, const double* __restrict__ lam, const double* __restrict__ x,
@@ -123,6 +196,132 @@ __global__ void __launch_bounds__(RED_THREADS) k_dot(size_t n, const double* __r
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
         v[0] += a[i] * b[i];
     if (grid_reduce<1>(v, partials, ticket, t)) *out = t[0];
+}
+
+// ---- BiCGStab for the pressure system (van der Vorst 1992, right-preconditioned) ----
+// Device scalars of one solve: every vector kernel reads them, the last block of each
+// reduction writes the ones it completes, and the host reads the block once per iteration.
+struct BicgScal {
+    double bb;              // <b, b>
+    double rho, rho_old;    // <r^, r> of this step and of the one before
+    double alpha, omega;
+    double ss, rr;          // <s, s>, <r, r>
+    double tol2bb;          // tol^2 <b, b>
+    int half;               // ||s|| <= tol ||b||: the step ends after its first half
+};
+
+// y = H z on the finest level from the premultiplied couplings a6 (diagonal form, FP64)
+__global__ void k_apply_a6(Lvl<double, double> L, const double* __restrict__ a6, const double* __restrict__ z,
+                           double* __restrict__ w) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x, k = blockIdx.y;
+    if (c >= L.ncol || k >= L.nlev) return;
+    const size_t ncol = L.ncol, N = (size_t)L.nlev * ncol, o = (size_t)k * ncol, e = o + c;
+    double we = __ldg(a6 + 6 * N + e) * __ldg(z + e);
+#pragma unroll
+    for (int s = 0; s < 4; ++s) we = fma(-__ldg(a6 + s * N + e), __ldg(z + o + __ldg(L.nbr + s * ncol + c)), we);
+    if (k + 1 < L.nlev) we = fma(-__ldg(a6 + 4 * N + e), __ldg(z + e + ncol), we);
+    if (k > 0) we = fma(-__ldg(a6 + 5 * N + e), __ldg(z + e - ncol), we);
+    w[e] = we;
+}
+
+#define MG_GRID_STRIDE(i, n) \
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < (n); i += (size_t)gridDim.x * blockDim.x)
+
+// r = r^ = b, x = 0; rho = <b, b>
+__global__ void __launch_bounds__(RED_THREADS) k_bicg_start(size_t n, const double* __restrict__ b, double* r,
+                                                            double* rh, double* x, double tol, double* partials,
+                                                            unsigned int* ticket, BicgScal* S) {
+    double v[1] = {0.0}, t[1];
+    MG_GRID_STRIDE(i, n) {
+        const double bi = b[i];
+        r[i] = bi;
+        rh[i] = bi;
+        x[i] = 0.0;
+        v[0] += bi * bi;
+    }
+    if (grid_reduce<1>(v, partials, ticket, t)) {
+        S->bb = t[0];
+        S->rho = t[0];
+        S->rho_old = 1.0;
+        S->alpha = 1.0;
+        S->omega = 1.0;
+        S->tol2bb = tol * tol * t[0];
+        S->half = 0;
+    }
+}
+
+// p = r (first step) or p = r + (rho / rho_old)(alpha / omega)(p - omega v)
+__global__ void k_bicg_dir(size_t n, const double* __restrict__ r, const double* __restrict__ v, double* p, bool first,
+                           const BicgScal* S) {
+    const double om = S->omega, beta = (S->rho / S->rho_old) * (S->alpha / om);
+    MG_GRID_STRIDE(i, n) p[i] = first ? r[i] : r[i] + beta * (p[i] - om * v[i]);
+}
+
+// alpha = rho / <r^, v>
+__global__ void __launch_bounds__(RED_THREADS) k_bicg_alpha(size_t n, const double* __restrict__ rh,
+                                                            const double* __restrict__ v, double* partials,
+                                                            unsigned int* ticket, BicgScal* S) {
+    double a[1] = {0.0}, t[1];
+    MG_GRID_STRIDE(i, n) a[0] += rh[i] * v[i];
+    if (grid_reduce<1>(a, partials, ticket, t)) S->alpha = S->rho / t[0];
+}
+
+// s = r - alpha v, <s, s>, and whether the step ends here
+__global__ void __launch_bounds__(RED_THREADS) k_bicg_s(size_t n, const double* __restrict__ r,
+                                                        const double* __restrict__ v, double* sv, double* partials,
+                                                        unsigned int* ticket, BicgScal* S) {
+    const double al = S->alpha;
+    double a[1] = {0.0}, t[1];
+    MG_GRID_STRIDE(i, n) {
+        const double si = r[i] - al * v[i];
+        sv[i] = si;
+        a[0] += si * si;
+    }
+    if (grid_reduce<1>(a, partials, ticket, t)) {
+        S->ss = t[0];
+        S->half = t[0] <= S->tol2bb;
+    }
+}
+
+// omega = <t, s> / <t, t>
+__global__ void __launch_bounds__(RED_THREADS) k_bicg_omega(size_t n, const double* __restrict__ tv,
+                                                            const double* __restrict__ sv, double* partials,
+                                                            unsigned int* ticket, BicgScal* S) {
+    double a[2] = {0.0, 0.0}, t[2];
+    MG_GRID_STRIDE(i, n) {
+        a[0] += tv[i] * sv[i];
+        a[1] += tv[i] * tv[i];
+    }
+    if (grid_reduce<2>(a, partials, ticket, t)) S->omega = t[0] / t[1];
+}
+
+// x += alpha p^ + omega s^, r = s - omega t (after a half step: x += alpha p^, r = s);
+// then rho_old = rho, rho = <r^, r>, rr = <r, r>
+__global__ void __launch_bounds__(RED_THREADS) k_bicg_xr(size_t n, double* x, double* r, const double* __restrict__ ph,
+                                                         const double* __restrict__ sh, const double* __restrict__ sv,
+                                                         const double* __restrict__ tv, const double* __restrict__ rh,
+                                                         double* partials, unsigned int* ticket, BicgScal* S) {
+    const double al = S->alpha, om = S->omega;
+    const bool half = S->half != 0;
+    double a[2] = {0.0, 0.0}, t[2];
+    MG_GRID_STRIDE(i, n) {
+        double ri;
+        if (half) {
+            x[i] += al * ph[i];
+            ri = sv[i];
+        } else {
+            x[i] += al * ph[i] + om * sh[i];
+            ri = sv[i] - om * tv[i];
+        }
+        r[i] = ri;
+        a[0] += rh[i] * ri;
+        a[1] += ri * ri;
+    }
+    if (grid_reduce<2>(a, partials, ticket, t)) {
+        S->rho_old = S->rho;
+        S->rho = t[0];
+        S->rr = t[1];
+    }
 }
 
 // GCR step coefficients for direction J (classical Gram-Schmidt, one pass):

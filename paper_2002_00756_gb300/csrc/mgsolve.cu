@@ -92,6 +92,12 @@ struct DevLevel {
     int sweep_bd = 0;          // threads per sweep block, a multiple of 64
     int restrict_kc = 0;       // levels per thread of the residual + restriction
     int restrict_async = -1;   // 1: copy-ring restriction (FP32 levels, n % 16 = 0), 0: register ring
+    // 9-cell stencil: fluxes two levels apart [nlev][ncol] and three scratch fields (the
+    // residual and the two Thomas factors of a sweep)
+    double* T2_64 = nullptr;
+    float* T2_32 = nullptr;
+    double* s64[3] = {nullptr, nullptr, nullptr};
+    float* s32[3] = {nullptr, nullptr, nullptr};
 };
 
 }  // namespace
@@ -105,9 +111,23 @@ struct mg_handle {
     double* rdz64 = nullptr;
     float* rdz32 = nullptr;
     double* a6 = nullptr;       // finest level: six premultiplied FP64 couplings and 1 + their sum, per cell
+    bool nine = false;          // 9-cell stencil (mg_setup_9pt)
     double* area0 = nullptr;    // finest level: column areas and layer depths (cell volumes, adjoint solve)
     double* dz = nullptr;
     double* adj = nullptr;      // [N] the scaled right-hand side of the adjoint solve
+    // finest-level face tables for caller-supplied couplings (mg_setup_coeffs, mg_set_coefficients)
+    int32_t* faceL0 = nullptr;
+    int32_t* faceR0 = nullptr;
+    int32_t* faceSide0 = nullptr;
+    int32_t* nbrSide0 = nullptr;
+    unsigned int* flag = nullptr;
+    // pressure solver K_H(A_H, P_H, eps_H) of the Schur-complement step (Sec. 4.1, Table 1)
+    mg_pressure_solver ps{MG_PS_MG, 1e-2, 0.8, 10, 200};
+    double* bv[8] = {};             // BiCGStab vectors r^, r, p, v, s, t, p^, s^ (allocated on demand)
+    mg::BicgScal* bs = nullptr;     // its device scalars
+    mg::BicgScal* host_bs = nullptr;   // pinned copy read once per iteration
+    long long ps_solves = 0;        // pressure solves since the last mg_inner_stats
+    double ps_iters = 0.0;          // their BiCGStab iterations (a half step counts 0.5)
     // GCR
     size_t glen = 0;            // length of a GCR vector (N, or nu + N with mixed data)
     double* Z = nullptr;        // [restart][glen]
@@ -150,7 +170,7 @@ struct mg_handle {
 
 namespace {
 
-enum { TK_DOT = 0, TK_SUMS, TK_ORTH, TK_COUNT };
+enum { TK_DOT = 0, TK_SUMS, TK_ORTH, TK_BICG, TK_COUNT };
 
 // k-chunk of the column kernels that have no vertical recurrence (apply): short chunks give
 // many independent threads, so the loads of different threads overlap
@@ -241,6 +261,8 @@ struct View<double, double> {
     static double* b(DevLevel& d) { return d.b64; }
     static double* r(DevLevel& d) { return d.r64; }
     static const double* w(const DevLevel& d) { return d.w64; }
+    static const double* t2(const DevLevel& d) { return d.T2_64; }
+    static double* scratch(DevLevel& d, int i) { return d.s64[i]; }
 };
 template <>
 struct View<float, float> {
@@ -252,6 +274,8 @@ struct View<float, float> {
     static float* b(DevLevel& d) { return d.b32; }
     static float* r(DevLevel& d) { return d.r32; }
     static const float* w(const DevLevel& d) { return d.w32; }
+    static const float* t2(const DevLevel& d) { return d.T2_32; }
+    static float* scratch(DevLevel& d, int i) { return d.s32[i]; }
 };
 template <>
 struct View<float, bf16> {
@@ -422,21 +446,34 @@ mg_status sweep_any(mg_handle* h, int lev, const Lvl<T, C>& L, const T* cur, con
     return launch_sweep<T, C, mg::XM_ZERO, T, B, O, false>(h, lev, L, cur, xc, ncol_c, b, bcopy, xo, om, s);
 }
 
+// Settings of one cycle: levels used, over-relaxation and sweep counts.  A single-level
+// cycle with n_coarse sweeps is the block-Jacobi iteration P_H^(Jac)(omega, n_coarse) of
+// Sec. 4.1 (line relaxation).
+struct Cycle {
+    int L;
+    double omega;
+    int n_pre, n_post, n_coarse;
+};
+
+inline Cycle vcycle_of(const mg_handle* h) {
+    return {h->L, h->prm.omega, h->prm.n_pre, h->prm.n_post, h->prm.n_coarse};
+}
+
 // Algorithm 1 on level l with right-hand side `b` (type B: FP64 on the finest level of the
 // FP32 V-cycle, T otherwise); the result goes to `out` (type O).  On every level the
 // iterate starts at zero (x^(l+1) <- 0 of Algorithm 1; the V-cycle is used as a
 // preconditioner, so x^(1) = 0 as well).
 template <typename T, typename C, typename B, typename O>
-mg_status mgv(mg_handle* h, int l, const B* b, O* out, cudaStream_t s) {
+mg_status mgv(mg_handle* h, const Cycle& cy, int l, const B* b, O* out, cudaStream_t s) {
     typedef View<T, C> V;
     DevLevel& d = h->lv[l];
     const Lvl<T, C> L = V::lvl(h, l);
-    const bool coarsest = (l == h->L - 1);
-    const double om = h->prm.omega;
+    const bool coarsest = (l == cy.L - 1);
+    const double om = cy.omega;
     const bool conv = !std::is_same<B, T>::value;  // rhs arrives in FP64, iterate in FP32
     T* ws[2] = {V::x(d, 0), V::x(d, 1)};
     const T* bT = conv ? (const T*)V::b(d) : (const T*)(const void*)b;
-    const int npre = coarsest ? h->prm.n_coarse : h->prm.n_pre;
+    const int npre = coarsest ? cy.n_coarse : cy.n_pre;
     if (conv && npre == 0) TRY(launch_convert(h, l, cells(h, l), b, V::b(d), s));
     T* cur = nullptr;
     for (int i = 0; i < npre; ++i) {
@@ -458,9 +495,9 @@ mg_status mgv(mg_handle* h, int l, const B* b, O* out, cudaStream_t s) {
     if (cur) TRY((launch_restrict<T, C, false, T, T, T>(h, l, L, cur, bT, V::w(d), bc, dc.ncol, s)));
     else TRY((launch_restrict<T, C, true, T, T, T>(h, l, L, cur, bT, V::w(d), bc, dc.ncol, s)));
     T* xc = V::r(dc);
-    TRY((mgv<T, C, T, T>(h, l + 1, bc, xc, s)));
+    TRY((mgv<T, C, T, T>(h, cy, l + 1, bc, xc, s)));
     // coarse-grid correction fused into the first post-smoothing sweep
-    const int npost = h->prm.n_post;
+    const int npost = cy.n_post;
     if (npost == 0) {
         if (cur) return launch_prolong<T, false, T, O>(h, l, d.n, d.ncol, dc.ncol, h->nlev, cur, xc, out, s);
         return launch_prolong<T, true, T, O>(h, l, d.n, d.ncol, dc.ncol, h->nlev, cur, xc, out, s);
@@ -476,13 +513,209 @@ mg_status mgv(mg_handle* h, int l, const B* b, O* out, cudaStream_t s) {
     return MG_OK;
 }
 
-mg_status run_vcycle(mg_handle* h, const double* b, double* x, cudaStream_t s) {
+// ---- the 9-cell stencil (Sec. 3.5): V-cycle with the tridiagonal smoother H_z-hat ----
+// x_out = x + omega Hz^-1 (b - H x), x == NULL meaning a zero iterate: the residual with the
+// full 9-cell stencil, then the column solves without the next-to-nearest fluxes
+template <typename T, typename B, typename O>
+mg_status sweep9(mg_handle* h, int lev, const T* x, const B* b, O* xo, double omega, cudaStream_t s) {
+    typedef View<T, T> V;
+    DevLevel& d = h->lv[lev];
+    const Lvl<T, T> L = V::lvl(h, lev);
+    Prof pr(h, MG_K_SWEEP, lev, (double)L.nlev * L.ncol * (sizeof(B) + 4.0 * sizeof(T) + sizeof(O) +
+                                                           (x ? 2.0 * sizeof(T) : 0.0)), s);
+    const dim3 g2((L.ncol + 127) / 128, L.nlev);
+    mg::k_resid9<T, B><<<g2, 128, 0, s>>>(L, V::t2(d), x, b, V::scratch(d, 0));
+    mg::k_thomas9<T, O><<<(L.ncol + 127) / 128, 128, 0, s>>>(L, V::scratch(d, 0), x, V::scratch(d, 1),
+                                                              V::scratch(d, 2), xo, (T)omega);
+    CK(cudaGetLastError());
+    return MG_OK;
+}
+
+// y = H x on level `lev` in FP64 for the 9-cell stencil
+mg_status launch_apply9(mg_handle* h, int lev, const double* x, double* y, cudaStream_t s) {
+    const Lvl<double, double> L = View<double, double>::lvl(h, lev);
+    Prof pr(h, MG_K_APPLY, lev, (double)L.nlev * L.ncol * 8.0 * 6, s);
+    mg::k_apply9<double, double, double><<<dim3((L.ncol + 127) / 128, L.nlev), 128, 0, s>>>(L, h->lv[lev].T2_64, x, y);
+    CK(cudaGetLastError());
+    return MG_OK;
+}
+
+// bc = Restrict(b - H x) onto level lev + 1 (9-cell stencil; x == NULL: zero iterate)
+template <typename T, typename B, typename O>
+mg_status restrict9(mg_handle* h, int lev, const T* x, const B* b, O* bc, cudaStream_t s) {
+    typedef View<T, T> V;
+    DevLevel& d = h->lv[lev];
+    const DevLevel& dc = h->lv[lev + 1];
+    const Lvl<T, T> L = V::lvl(h, lev);
+    Prof pr(h, MG_K_RESTRICT, lev, (double)L.nlev * L.ncol * (sizeof(B) + 2.0 * sizeof(T) + 0.25 * sizeof(O)), s);
+    const dim3 g2((L.ncol + 127) / 128, L.nlev);
+    mg::k_resid9<T, B><<<g2, 128, 0, s>>>(L, V::t2(d), x, b, V::scratch(d, 0));
+    mg::k_restrict_sum<T, O><<<dim3((dc.ncol + 127) / 128, L.nlev), 128, 0, s>>>(d.n, d.ncol, L.nlev, V::scratch(d, 0),
+                                                                               V::w(d), bc, dc.ncol);
+    CK(cudaGetLastError());
+    return MG_OK;
+}
+
+// Algorithm 1 for the 9-cell stencil: the same steps as mgv, each a plain kernel (the
+// right-hand side converted on entry and the result on exit in the FP32 variant)
+template <typename T, typename B, typename O>
+mg_status mgv9(mg_handle* h, const Cycle& cy, int l, const B* b, O* out, cudaStream_t s) {
+    typedef View<T, T> V;
+    DevLevel& d = h->lv[l];
+    const size_t n = cells(h, l);
+    const bool coarsest = (l == cy.L - 1);
+    const double om = cy.omega;
+    const T* bT = (const T*)(const void*)b;
+    if (!std::is_same<B, T>::value) {
+        TRY(launch_convert(h, l, n, b, V::b(d), s));
+        bT = V::b(d);
+    }
+    T* ws[2] = {V::x(d, 0), V::x(d, 1)};
+    T* cur = nullptr;
+    auto other = [&]() { return cur == ws[0] ? ws[1] : ws[0]; };
+    const int npre = coarsest ? cy.n_coarse : cy.n_pre;
+    for (int i = 0; i < npre; ++i) {
+        T* dst = other();
+        TRY((sweep9<T, T, T>(h, l, cur, bT, dst, om, s)));
+        cur = dst;
+    }
+    if (!coarsest) {
+        DevLevel& dc = h->lv[l + 1];
+        TRY((restrict9<T, T, T>(h, l, cur, bT, V::b(dc), s)));
+        T* xc = V::r(dc);
+        TRY((mgv9<T, T, T>(h, cy, l + 1, V::b(dc), xc, s)));
+        T* dst = other();
+        if (cur) TRY((launch_prolong<T, false, T, T>(h, l, d.n, d.ncol, dc.ncol, h->nlev, cur, xc, dst, s)));
+        else TRY((launch_prolong<T, true, T, T>(h, l, d.n, d.ncol, dc.ncol, h->nlev, cur, xc, dst, s)));
+        cur = dst;
+        for (int i = 0; i < cy.n_post; ++i) {
+            T* dst2 = other();
+            TRY((sweep9<T, T, T>(h, l, cur, bT, dst2, om, s)));
+            cur = dst2;
+        }
+    }
+    if (!cur) {
+        CK(cudaMemsetAsync(out, 0, n * sizeof(O), s));
+        return MG_OK;
+    }
+    return launch_convert(h, l, n, (const T*)cur, out, s);
+}
+
+mg_status run_cycle(mg_handle* h, const Cycle& cy, const double* b, double* x, cudaStream_t s) {
+    if (h->nine) {
+        switch (h->prm.vcycle_precision) {
+            case MG_FP64: return mgv9<double, double, double>(h, cy, 0, b, x, s);
+            case MG_FP32: return mgv9<float, double, double>(h, cy, 0, b, x, s);
+            default: return MG_ERR_UNSUPPORTED;
+        }
+    }
     switch (h->prm.vcycle_precision) {
-        case MG_FP64: return mgv<double, double, double, double>(h, 0, b, x, s);
-        case MG_FP32: return mgv<float, float, double, double>(h, 0, b, x, s);
-        case MG_FP32_BF16COEF: return mgv<float, bf16, double, double>(h, 0, b, x, s);
+        case MG_FP64: return mgv<double, double, double, double>(h, cy, 0, b, x, s);
+        case MG_FP32: return mgv<float, float, double, double>(h, cy, 0, b, x, s);
+        case MG_FP32_BF16COEF: return mgv<float, bf16, double, double>(h, cy, 0, b, x, s);
         default: return MG_ERR_ARG;
     }
+}
+
+mg_status run_vcycle(mg_handle* h, const double* b, double* x, cudaStream_t s) {
+    return run_cycle(h, vcycle_of(h), b, x, s);
+}
+
+// P_H^(Jac)(omega, n) of Sec. 4.1: n block-Jacobi sweeps from zero on the finest level, in the
+// handle's V-cycle precision (a one-level cycle)
+mg_status run_jacobi(mg_handle* h, double omega, int sweeps, const double* b, double* x, cudaStream_t s) {
+    return run_cycle(h, Cycle{1, omega, 0, 0, sweeps}, b, x, s);
+}
+
+// BiCGStab(H, P, tol) on the finest level (Sec. 4.1 solver list; Table 1 "Krylov" rows) from
+// x = 0: the vector updates and inner products run in the kernels above with device scalars;
+// the host reads them once per iteration to test convergence.  *iters counts a half step as 0.5.
+template <typename Pre>
+mg_status bicgstab(mg_handle* h, const double* b, double* x, double tol, int maxit, Pre& P, cudaStream_t s,
+                   double* iters) {
+    const size_t n = cells(h, 0);
+    double *rh = h->bv[0], *r = h->bv[1], *p = h->bv[2], *v = h->bv[3], *sv = h->bv[4], *t = h->bv[5],
+           *ph = h->bv[6], *sh = h->bv[7];
+    if (!rh) return MG_ERR_UNSUPPORTED;
+    const Lvl<double, double> L = View<double, double>::lvl(h, 0);
+    const dim3 ag((L.ncol + 127) / 128, L.nlev);
+    const int G = h->red_grid, B = mg::RED_THREADS;
+    unsigned int* tk = h->tickets + TK_BICG;
+    auto apply = [&](const double* in, double* out) -> mg_status {
+        if (h->nine) return launch_apply9(h, 0, in, out, s);
+        Prof pr(h, MG_K_APPLY, 0, 8.0 * n * 9, s);
+        mg::k_apply_a6<<<ag, 128, 0, s>>>(L, h->a6, in, out);
+        CK(cudaGetLastError());
+        return MG_OK;
+    };
+    *iters = 0.0;
+    mg::k_bicg_start<<<G, B, 0, s>>>(n, b, r, rh, x, tol, h->partials, tk, h->bs);
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(h->host_bs, h->bs, sizeof(mg::BicgScal), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (!std::isfinite(h->host_bs->bb)) return MG_ERR_BREAKDOWN;
+    if (h->host_bs->bb == 0.0) return MG_OK;
+    for (int i = 0; i < maxit; ++i) {
+        mg::k_bicg_dir<<<G, B, 0, s>>>(n, r, v, p, i == 0, h->bs);
+        CK(cudaGetLastError());
+        TRY(P(p, ph));
+        TRY(apply(ph, v));
+        mg::k_bicg_alpha<<<G, B, 0, s>>>(n, rh, v, h->partials, tk, h->bs);
+        mg::k_bicg_s<<<G, B, 0, s>>>(n, r, v, sv, h->partials, tk, h->bs);
+        CK(cudaGetLastError());
+        TRY(P(sv, sh));
+        TRY(apply(sh, t));
+        mg::k_bicg_omega<<<G, B, 0, s>>>(n, t, sv, h->partials, tk, h->bs);
+        mg::k_bicg_xr<<<G, B, 0, s>>>(n, x, r, ph, sh, sv, t, rh, h->partials, tk, h->bs);
+        CK(cudaGetLastError());
+        CK(cudaMemcpyAsync(h->host_bs, h->bs, sizeof(mg::BicgScal), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        const mg::BicgScal& S = *h->host_bs;
+        if (!std::isfinite(S.alpha) || !std::isfinite(S.ss)) return MG_ERR_BREAKDOWN;
+        if (S.half) {
+            *iters = i + 0.5;
+            return MG_OK;
+        }
+        if (!std::isfinite(S.omega) || !std::isfinite(S.rr) || !std::isfinite(S.rho)) return MG_ERR_BREAKDOWN;
+        *iters = i + 1.0;
+        if (S.rr <= S.tol2bb) return MG_OK;
+        if (S.omega == 0.0 || S.rho == 0.0) return MG_ERR_BREAKDOWN;
+    }
+    return MG_ERR_NOT_CONVERGED;
+}
+
+// x ~ H^-1 b by the handle's pressure solver: one V-cycle (MG(L)), line relaxation, or
+// BiCGStab to eps_H preconditioned by one of the two (Table 1); *iters as for bicgstab
+mg_status run_pressure_solver(mg_handle* h, const double* b, double* x, cudaStream_t s, double* iters) {
+    const mg_pressure_solver& ps = h->ps;
+    *iters = 0.0;
+    mg_status st = MG_OK;
+    switch (ps.kind) {
+        case MG_PS_MG: st = run_vcycle(h, b, x, s); break;
+        case MG_PS_JACOBI: st = run_jacobi(h, ps.omega, ps.sweeps, b, x, s); break;
+        case MG_PS_BICGSTAB_JACOBI: {
+            auto P = [&](const double* in, double* out) { return run_jacobi(h, ps.omega, ps.sweeps, in, out, s); };
+            st = bicgstab(h, b, x, ps.eps, ps.max_iter, P, s, iters);
+            break;
+        }
+        case MG_PS_BICGSTAB_MG: {
+            auto P = [&](const double* in, double* out) { return run_vcycle(h, in, out, s); };
+            st = bicgstab(h, b, x, ps.eps, ps.max_iter, P, s, iters);
+            break;
+        }
+        default: return MG_ERR_ARG;
+    }
+    if (ps.kind == MG_PS_BICGSTAB_JACOBI || ps.kind == MG_PS_BICGSTAB_MG) {
+        h->ps_solves += 1;
+        h->ps_iters += *iters;
+    }
+    return st;
+}
+
+// the pressure solver synchronises with the host (BiCGStab): the mixed GCR then launches its
+// iterations directly instead of capturing them into graphs
+inline bool ps_syncs(const mg_handle* h) {
+    return h->ps.kind == MG_PS_BICGSTAB_JACOBI || h->ps.kind == MG_PS_BICGSTAB_MG;
 }
 
 // ---- GCR (Sec. 4.1; textbook generalised conjugate residual, right preconditioned) ----
@@ -559,6 +792,10 @@ mg_status gcr_sums(mg_handle* h, size_t n, const double* w, int j, cudaStream_t 
 }
 
 mg_status apply_gcr(mg_handle* h, const double* z, double* w, int j, cudaStream_t s) {
+    if (h->nine) {
+        TRY(launch_apply9(h, 0, z, w, s));
+        return gcr_sums(h, cells(h, 0), w, j, s);
+    }
     return dispatch_j<RunApplyGcr>(j, h, z, w, s);
 }
 
@@ -640,8 +877,9 @@ mg_status gcr_launch(mg_handle* h, GcrRun& g, cudaStream_t s, ApplyAS& applyAS, 
         return MG_OK;
     };
     cudaGraphExec_t& ge = h->gexec[g.sys][j];
-    if (!ge && !h->prof && !h->graphs_off) capture_graph(h, body, &ge);
-    if (ge && !h->prof) CK(cudaGraphLaunch(ge, s));
+    const bool direct = h->prof || (g.sys != 0 && ps_syncs(h));
+    if (!ge && !direct && !h->graphs_off) capture_graph(h, body, &ge);
+    if (ge && !direct) CK(cudaGraphLaunch(ge, s));
     else TRY(body(s));
     return MG_OK;
 }
@@ -739,12 +977,44 @@ mg_status schur_impl(mg_handle* h, const double* ru, const double* rp, double* u
     // Step 1: B = r_p - D M-ring^{-1} r_u
     mg::k_mx_cells<1><<<dim3((M.ncol + bd - 1) / bd, M.nlev), bd, 0, s>>>(M, ru, ru + nh, rp, h->schurB);
     CK(cudaGetLastError());
-    // Step 2: one V-cycle for H Pi' = B
-    TRY(run_vcycle(h, h->schurB, p, s));
+    // Step 2: H Pi' = B by the pressure solver K_H(A_H, P_H, eps_H) (one V-cycle by default);
+    // an inexact inner solve (BiCGStab at its iteration limit) is still a usable preconditioner
+    double it = 0.0;
+    const mg_status st = run_pressure_solver(h, h->schurB, p, s, &it);
+    if (st != MG_OK && st != MG_ERR_NOT_CONVERGED) return st;
     // Step 3: u' = M-ring^{-1} (r_u - G Pi')
     mg::k_mx_faces_h<1><<<dim3((M.nfh + bd - 1) / bd, M.nlev), bd, 0, s>>>(M, ru, p, u);
     mg::k_mx_faces_v<1><<<dim3((M.ncol + bd - 1) / bd, M.nlev + 1), bd, 0, s>>>(M, ru + nh, p, u + nh);
     CK(cudaGetLastError());
+    return MG_OK;
+}
+
+// Replaces the finest-level operator by the caller's couplings a[s][k][c] (DEVICE, 6 N): the
+// FP64 operator of the GCR apply takes them as they are, the V-cycle's finest level their face
+// form in its precision.  A first pass only checks them (flux symmetry, sign, no flux through
+// surface and lid); the operator is changed only if every check passes.
+mg_status set_coefficients_impl(mg_handle* h, const double* a, cudaStream_t s) {
+    const int ncol = h->lv[0].ncol, nlev = h->nlev, nf = 2 * ncol;
+    const DevLevel& d = h->lv[0];
+    const mg::CoefTargets t{d.Th64, d.Th32, d.Th16, d.Tv64, d.Tv32, d.Tv16};
+    CK(cudaMemsetAsync(h->flag, 0, sizeof(unsigned int), s));
+    for (int pass = 0; pass < 2; ++pass) {
+        const bool write = pass == 1;
+        mg::k_coef_faces<<<dim3((nf + 127) / 128, nlev), 128, 0, s>>>(ncol, nlev, h->faceL0, h->faceR0, h->faceSide0,
+                                                                       h->nbrSide0, h->area0, a, write, t, h->flag);
+        mg::k_coef_vertical<<<dim3((ncol + 127) / 128, nlev + 1), 128, 0, s>>>(ncol, nlev, h->dz, a, write, t,
+                                                                                h->flag);
+        CK(cudaGetLastError());
+        if (!write) {
+            unsigned int bad = 0;
+            CK(cudaMemcpyAsync(&bad, h->flag, sizeof bad, cudaMemcpyDeviceToHost, s));
+            CK(cudaStreamSynchronize(s));
+            if (bad) return MG_ERR_ARG;
+        }
+    }
+    mg::k_coef_cells<<<4 * h->nsm, 256, 0, s>>>(cells(h, 0), a, h->a6);
+    CK(cudaGetLastError());
+    CK(cudaStreamSynchronize(s));
     return MG_OK;
 }
 
@@ -815,7 +1085,7 @@ void horizontal_mass(const mg::HGeom& G, bool consistent, double f0, HMass& hm) 
 }
 
 mg_status setup_impl(mg_handle* h, const mg_mesh* mesh, const mg_params* prm, const double* g,
-                     const mg_mixed* mixed) {
+                     const mg_mixed* mixed, double gamma2 = 0.0) {
     const int L = prm->levels, n = mesh->n, nlev = mesh->nlev;
     h->L = L;
     h->n = n;
@@ -879,6 +1149,11 @@ mg_status setup_impl(mg_handle* h, const mg_mesh* mesh, const mg_params* prm, co
     TRY(upload(h, &h->dz, vg.dz));
     TRY(upload(h, &h->area0, hg[0].area));
     TRY(upload(h, &h->rdz32, rdz));
+    TRY(upload(h, &h->faceL0, hg[0].faceL));
+    TRY(upload(h, &h->faceR0, hg[0].faceR));
+    TRY(upload(h, &h->faceSide0, hg[0].faceSide));
+    TRY(upload(h, &h->nbrSide0, hg[0].nbr_side));
+    TRY(dalloc(h, &h->flag, 1));
     const int prec = prm->vcycle_precision;
     h->lv.resize(L);
     for (int l = 0; l < L; ++l) {
@@ -911,6 +1186,27 @@ mg_status setup_impl(mg_handle* h, const mg_mesh* mesh, const mg_params* prm, co
             TRY(dalloc(h, &d.x32[1], Nl));
             TRY(dalloc(h, &d.b32, Nl));
             TRY(dalloc(h, &d.r32, Nl));
+        }
+        if (gamma2 > 0.0) {
+            // 9-cell stencil: flux between cells k and k + 2 of every column,
+            // gamma2 (c_s dt)^2 (g_k + g_k+2) / 2 / (z_c[k+2] - z_c[k])
+            h->nine = true;
+            std::vector<double> t2(Nl, 0.0);
+            const double c2 = mesh->cs_dt * mesh->cs_dt;
+            const double* z = mesh->z_interfaces;
+            for (int k = 0; k + 2 < nlev; ++k) {
+                const double dzc2 = 0.5 * (z[k + 3] + z[k + 2]) - 0.5 * (z[k + 1] + z[k]);
+                for (int c = 0; c < G.ncol; ++c)
+                    t2[(size_t)k * G.ncol + c] =
+                        gamma2 * c2 * 0.5 * (co[l].g[(size_t)k * G.ncol + c] + co[l].g[(size_t)(k + 2) * G.ncol + c]) /
+                        dzc2;
+            }
+            TRY(upload(h, &d.T2_64, t2));
+            for (double*& p : d.s64) TRY(dalloc(h, &p, Nl));
+            if (prec == MG_FP32) {
+                TRY(upload(h, &d.T2_32, t2));
+                for (float*& p : d.s32) TRY(dalloc(h, &p, Nl));
+            }
         }
         if (l + 1 < L) {
             const mg::HGeom& Gc = hg[l + 1];
@@ -1049,6 +1345,8 @@ mg_status setup_impl(mg_handle* h, const mg_mesh* mesh, const mg_params* prm, co
     CK(cudaMemset(h->tickets, 0, TK_COUNT * sizeof(unsigned int)));
     CK(cudaMemset(h->gs, 0, sizeof(mg::GcrScal)));
     if (cudaMallocHost(&h->host_sc, 4 * sizeof(double)) != cudaSuccess) return MG_ERR_NOMEM;
+    if (cudaMallocHost(&h->host_bs, sizeof(mg::BicgScal)) != cudaSuccess) return MG_ERR_NOMEM;
+    TRY(dalloc(h, &h->bs, 1));
     CK(cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking));
     CK(cudaStreamCreateWithFlags(&h->run, cudaStreamNonBlocking));
     CK(cudaEventCreateWithFlags(&h->evx, cudaEventDisableTiming));
@@ -1062,6 +1360,7 @@ void free_handle(mg_handle* h) {
     if (!h) return;
     for (void* p : h->allocs) cudaFree(p);
     if (h->host_sc) cudaFreeHost(h->host_sc);
+    if (h->host_bs) cudaFreeHost(h->host_bs);
     for (auto& row : h->gexec)
         for (cudaGraphExec_t g : row)
             if (g) cudaGraphExecDestroy(g);
@@ -1077,6 +1376,8 @@ void free_handle(mg_handle* h) {
 }  // namespace
 
 // =====================================================================================
+static mg_status mg_setup_check(const mg_mesh* mesh, const mg_params* prm, const double* g, const mg_mixed* mixed);
+
 extern "C" {
 
 const char* mg_status_string(mg_status s) {
@@ -1097,6 +1398,21 @@ mg_status mg_setup(const mg_mesh* mesh, const mg_params* prm, const double* g, c
                    mg_handle** out) {
     if (!out) return MG_ERR_ARG;
     *out = nullptr;
+    TRY(mg_setup_check(mesh, prm, g, mixed));
+    mg_handle* h = new (std::nothrow) mg_handle();
+    if (!h) return MG_ERR_NOMEM;
+    mg_status st = setup_impl(h, mesh, prm, g, mixed);
+    if (st != MG_OK) {
+        free_handle(h);
+        return st;
+    }
+    *out = h;
+    return MG_OK;
+}
+
+}  // extern "C"
+
+static mg_status mg_setup_check(const mg_mesh* mesh, const mg_params* prm, const double* g, const mg_mixed* mixed) {
     if (!mesh || !prm || !g || !mesh->z_interfaces) return MG_ERR_ARG;
     if (mesh->n < 1 || mesh->nlev < 1 || mesh->nlev > MG_MAX_NLEV) return MG_ERR_ARG;
     if (!(mesh->radius > 0.0) || !(mesh->cs_dt > 0.0) || !std::isfinite(mesh->cs_dt)) return MG_ERR_ARG;
@@ -1111,15 +1427,106 @@ mg_status mg_setup(const mg_mesh* mesh, const mg_params* prm, const double* g, c
         return MG_ERR_ARG;
     // the column kernels address a level with 32-bit offsets (horizontal faces: 2 kc)
     if (2.0 * (mesh->nlev + 1) * 6.0 * (double)mesh->n * mesh->n >= 4294967296.0) return MG_ERR_UNSUPPORTED;
-    mg_handle* h = new (std::nothrow) mg_handle();
+    return MG_OK;
+}
+
+extern "C" {
+
+mg_status mg_setup_9pt(const mg_mesh* mesh, const mg_params* prm, const double* g, double gamma2, mg_handle** out) {
+    if (!out) return MG_ERR_ARG;
+    *out = nullptr;
+    if (!(gamma2 > 0.0) || !std::isfinite(gamma2) || !prm) return MG_ERR_ARG;
+    if (prm->vcycle_precision == MG_FP32_BF16COEF) return MG_ERR_UNSUPPORTED;
+    if (!mesh || !g || !mesh->z_interfaces) return MG_ERR_ARG;
+    mg_handle* h = nullptr;
+    // validate exactly as mg_setup does, then build with the next-to-nearest fluxes
+    TRY(mg_setup_check(mesh, prm, g, nullptr));
+    h = new (std::nothrow) mg_handle();
     if (!h) return MG_ERR_NOMEM;
-    mg_status st = setup_impl(h, mesh, prm, g, mixed);
+    const mg_status st = setup_impl(h, mesh, prm, g, nullptr, gamma2);
     if (st != MG_OK) {
         free_handle(h);
         return st;
     }
     *out = h;
     return MG_OK;
+}
+
+mg_status mg_setup_coeffs(const mg_mesh* mesh, const mg_params* prm, const double* coeffs, const double* cell_factors,
+                          mg_handle** out) {
+    if (!out) return MG_ERR_ARG;
+    *out = nullptr;
+    if (!coeffs) return MG_ERR_ARG;
+    mg_handle* h = nullptr;
+    TRY(mg_setup(mesh, prm, cell_factors, nullptr, &h));
+    const size_t n6 = 6 * cells(h, 0);
+    double* tmp = nullptr;
+    mg_status st = MG_OK;
+    if (cudaMalloc(&tmp, n6 * sizeof(double)) != cudaSuccess) {
+        cudaGetLastError();
+        st = MG_ERR_NOMEM;
+    } else if (cudaMemcpy(tmp, coeffs, n6 * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess) {
+        st = MG_ERR_CUDA;
+    } else {
+        st = set_coefficients_impl(h, tmp, nullptr);
+        if (st == MG_OK && cudaDeviceSynchronize() != cudaSuccess) st = MG_ERR_CUDA;
+    }
+    if (tmp) cudaFree(tmp);
+    if (st != MG_OK) {
+        mg_destroy(h);
+        return st;
+    }
+    *out = h;
+    return MG_OK;
+}
+
+mg_status mg_set_pressure_solver(mg_handle* h, const mg_pressure_solver* ps) {
+    if (!h || !ps) return MG_ERR_ARG;
+    if (ps->kind < MG_PS_MG || ps->kind > MG_PS_BICGSTAB_MG) return MG_ERR_ARG;
+    const bool jac = ps->kind == MG_PS_JACOBI || ps->kind == MG_PS_BICGSTAB_JACOBI;
+    const bool bicg = ps->kind == MG_PS_BICGSTAB_JACOBI || ps->kind == MG_PS_BICGSTAB_MG;
+    if (jac && (ps->sweeps < 1 || !std::isfinite(ps->omega))) return MG_ERR_ARG;
+    if (bicg && (!(ps->eps >= 0.0) || ps->max_iter < 1)) return MG_ERR_ARG;
+    DeviceGuard dg(h->device);
+    if (bicg && !h->bv[0]) {
+        const size_t n = cells(h, 0);
+        for (double*& v : h->bv) TRY(dalloc(h, &v, n));
+    }
+    CK(cudaDeviceSynchronize());
+    h->ps = *ps;
+    // the cached mixed-solve graphs hold the previous pressure solver
+    for (int sys = 1; sys < 3; ++sys)
+        for (cudaGraphExec_t& g : h->gexec[sys])
+            if (g) {
+                cudaGraphExecDestroy(g);
+                g = nullptr;
+            }
+    return MG_OK;
+}
+
+mg_status helmholtz_solve(mg_handle* h, const double* b, double* x, double* iterations, void* stream) {
+    if (!h || !b || !x || b == x) return MG_ERR_ARG;
+    DeviceGuard dg(h->device);
+    double it = 0.0;
+    const mg_status st = run_pressure_solver(h, b, x, S(stream), &it);
+    if (iterations) *iterations = it;
+    return st;
+}
+
+mg_status mg_inner_stats(mg_handle* h, int64_t* solves, double* iterations) {
+    if (!h) return MG_ERR_ARG;
+    if (solves) *solves = h->ps_solves;
+    if (iterations) *iterations = h->ps_iters;
+    h->ps_solves = 0;
+    h->ps_iters = 0.0;
+    return MG_OK;
+}
+
+mg_status mg_set_coefficients(mg_handle* h, const double* coeffs, void* stream) {
+    if (!h || !coeffs) return MG_ERR_ARG;
+    if (h->mixed || h->nine) return MG_ERR_UNSUPPORTED;
+    DeviceGuard dg(h->device);
+    return set_coefficients_impl(h, coeffs, S(stream));
 }
 
 void mg_destroy(mg_handle* h) {
@@ -1140,6 +1547,7 @@ mg_status mg_sizes(const mg_handle* h, int64_t* ncol, int64_t* ncell, int64_t* n
 mg_status helmholtz_apply(mg_handle* h, const double* x, double* y, void* stream) {
     if (!h || !x || !y || x == y) return MG_ERR_ARG;
     DeviceGuard dg(h->device);
+    if (h->nine) return launch_apply9(h, 0, x, y, S(stream));
     return launch_apply(h, 0, View<double, double>::lvl(h, 0), x, y, S(stream));
 }
 
@@ -1188,6 +1596,7 @@ mg_status pressure_solve_adjoint(mg_handle* h, const double* g, double* lambda, 
 mg_status helmholtz_coefficient_gradient(mg_handle* h, const double* lambda, const double* x, double* grad,
                                          void* stream) {
     if (!h || !lambda || !x || !grad) return MG_ERR_ARG;
+    if (h->nine) return MG_ERR_UNSUPPORTED;
     DeviceGuard dg(h->device);
     cudaStream_t s = S(stream);
     const Lvl<double, double> L = View<double, double>::lvl(h, 0);
@@ -1333,6 +1742,7 @@ mg_status mg_level_apply(mg_handle* h, int32_t level, const double* x, double* y
     TRY(check_level(h, level));
     if (!x || !y || x == y) return MG_ERR_ARG;
     DeviceGuard dg(h->device);
+    if (h->nine) return launch_apply9(h, level, x, y, S(stream));
     return launch_apply(h, level, View<double, double>::lvl(h, level), x, y, S(stream));
 }
 
@@ -1348,8 +1758,9 @@ mg_status mg_smooth(mg_handle* h, int32_t level, const double* b, const double* 
     const double* cur = x_in;
     for (int i = 0; i < sweeps; ++i) {
         double* dst = (cur == d.x64[0]) ? d.x64[1] : d.x64[0];
-        TRY((sweep_any<double, double, double, double>(h, level, L, cur, (const double*)nullptr, 0, b, nullptr, dst,
-                                                       h->prm.omega, s)));
+        if (h->nine) TRY((sweep9<double, double, double>(h, level, cur, b, dst, h->prm.omega, s)));
+        else TRY((sweep_any<double, double, double, double>(h, level, L, cur, (const double*)nullptr, 0, b, nullptr,
+                                                            dst, h->prm.omega, s)));
         cur = dst;
     }
     if (cur == nullptr) CK(cudaMemsetAsync(x_out, 0, n * sizeof(double), s));
@@ -1362,6 +1773,7 @@ mg_status mg_residual_restrict(mg_handle* h, int32_t level, const double* b, con
     TRY(check_level(h, level));
     if (level + 1 >= h->L || !b || !x || !bc) return MG_ERR_ARG;
     DeviceGuard dg(h->device);
+    if (h->nine) return restrict9<double, double, double>(h, level, x, b, bc, S(stream));
     return launch_restrict<double, double, false, double, double, double>(
         h, level, View<double, double>::lvl(h, level), x, b, h->lv[level].w64, bc, h->lv[level + 1].ncol, S(stream));
 }
@@ -1391,7 +1803,7 @@ mg_status schur_precond(mg_handle* h, const double* ru, const double* rp, double
 
 mg_status mg_autotune(mg_handle* h, int32_t* choices, void* stream) {
     if (!h) return MG_ERR_ARG;
-    if (h->prof) return MG_ERR_UNSUPPORTED;   // the tuner uses the per-launch profiler itself
+    if (h->prof || h->nine) return MG_ERR_UNSUPPORTED;   // the tuner uses the per-launch profiler itself
     DeviceGuard dg(h->device);
     cudaStream_t s = S(stream);
     const int L = h->L;
@@ -1545,6 +1957,7 @@ extern "C" mg_status mg_smooth_noalloc(mg_handle* h, int32_t level, const double
                                        double* x_out, int32_t sweeps, void* stream) {
     TRY(check_level(h, level));
     if (!b || !x_out || sweeps < 0 || b == x_out) return MG_ERR_ARG;
+    if (h->nine) return MG_ERR_UNSUPPORTED;
     const size_t n = cells(h, level);
     if (n > (size_t)MG_NOALLOC_MAX_CELLS) return MG_ERR_ARG;
     DeviceGuard dg(h->device);

@@ -254,7 +254,7 @@ def test_solver_status_paths(mg):
     with pytest.raises(mg.MGError):
         mg.vcycle(h2, bad, bad)
     u = torch.zeros(10, dtype=torch.float64, device="cuda")
-    assert mg.load().mixed_solve(h2.ptr, mg._ptr(u), mg._ptr(u), mg._ptr(u), mg._ptr(u), 1e-8, None,
+    assert mg.load().mixed_solve(h2.ptr, mg._raw_ptr(u), mg._raw_ptr(u), mg._raw_ptr(u), mg._raw_ptr(u), 1e-8, None,
                                  mg._stream(None)) == mg.MG_ERR_UNSUPPORTED
 
 

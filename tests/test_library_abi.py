@@ -109,6 +109,10 @@ def test_null_handle_calls_are_rejected(lib):
     assert lib.ensemble_pressure_solve(None, 1, None, None, 1e-8, None, None, None) == -1
     hs = (ctypes.c_void_p * 1)(None)
     assert lib.ensemble_pressure_solve(hs, 1, hs, hs, 1e-8, None, None, None) == -1     # NULL member
+    assert lib.mg_set_coefficients(None, vp(8), None) == -1
+    out = ctypes.c_void_p()
+    assert lib.mg_setup_coeffs(None, None, None, None, ctypes.byref(out)) == -1 and not out.value
+    assert lib.mg_setup_coeffs(None, None, None, None, None) == -1
     lib.mg_destroy(None)
 
 
@@ -139,6 +143,8 @@ def test_binding_rejects_host_and_mistyped_vectors(lib):
         lambda: mg.mixed_coefficient_gradient(h, u, u, c, c, v, v),
         lambda: mg.mg_smooth(h, 0, c, c, c, 1),
         lambda: mg.mg_smooth_noalloc(h, 0, c, c, c, 1),
+        lambda: mg.mg_set_coefficients(h, torch.zeros(6 * h.ncell, dtype=torch.float64)),
+        lambda: mg.solve(h, c),
     ]
     try:
         for call in calls:
@@ -147,6 +153,6 @@ def test_binding_rejects_host_and_mistyped_vectors(lib):
     finally:
         h._ptr = ctypes.c_void_p(None)
     with pytest.raises(TypeError):
-        mg._ptr(torch.zeros(4, dtype=torch.float32), 4)
+        mg._raw_ptr(torch.zeros(4, dtype=torch.float32), 4)
     with pytest.raises(ValueError, match="expected 4"):
         mg._host(np.zeros(5), 4, "x")

@@ -1,7 +1,7 @@
 """mg_smooth_noalloc: block-Jacobi smoothing for callers that cannot allocate device memory.
 
-Callers recording a CUDA graph, running a real-time loop or living inside a framework
-whose memory pool owns the device cannot call cudaMalloc when they smooth; this entry
+Callers running a real-time loop, living inside a framework whose memory pool owns the
+device or held to a fixed device-memory budget cannot call cudaMalloc when they smooth; this entry
 point keeps its intermediate iterate in a fixed device array inside the library instead.
 The test calls it through the C ABI and compares it with mg_smooth (same kernels, so the
 results agree to the parity tolerance of the other tests, 1e-12 relative), twice in a
