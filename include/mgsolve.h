@@ -277,6 +277,39 @@ mg_status ensemble_pressure_solve(mg_handle* const* handles, int32_t count, cons
                                   double* const* x, double tol, mg_solve_info* infos, int32_t* statuses,
                                   void* stream);
 
+/* ---- an ensemble of pressure solves as ONE graph launch ----
+ * mg_ensemble_create records, once, the whole of every member's pressure_solve into one CUDA
+ * graph: per member the start (r = b, x = 0, <b, b>), then a conditional WHILE node whose body
+ * holds one conditional IF node per GCR restart slot j (the V-cycle, the fused apply and the
+ * orthogonalisation of slot j, then a single-thread kernel that takes the convergence,
+ * iteration-limit and breakdown decisions the host takes in pressure_solve) and one IF node for
+ * the solution update that closes a restart cycle.  The members are independent branches of the
+ * graph, so members of different meshes, level counts and precisions run side by side, and
+ * every decision stays on the device: mg_ensemble_solve is one cudaGraphLaunch followed by one
+ * stream synchronisation.  Each member gets exactly what pressure_solve gives it alone (the same
+ * kernels in the same order, the same FP64 decisions): the same x bit for bit, the same
+ * iteration count and status.  No device-side wait is involved (the conditions are set by a
+ * kernel that precedes the nodes reading them).
+ *   handles   count distinct pressure handles (no mixed data, not profiling) of one device
+ *   b, x      count DEVICE pointers, N_i doubles each (x[i] != b[i]); recorded into the graph, so
+ *             every solve reads b[i] and writes x[i] at these addresses (refill b between solves)
+ *   tol       relative residual of every member
+ * The handles must outlive the ensemble and must not be used by other calls while
+ * mg_ensemble_solve runs; launch shapes chosen by a later mg_autotune are not picked up
+ * (create the ensemble after tuning).  Synchronous.  MG_ERR_UNSUPPORTED for a mixed or
+ * profiling handle. */
+typedef struct mg_ensemble mg_ensemble;
+mg_status mg_ensemble_create(mg_handle* const* handles, int32_t count, const double* const* b, double* const* x,
+                             double tol, mg_ensemble** out);
+
+/* Run every member once (one graph launch, then one synchronisation of `stream`).  infos (may be
+ * NULL, count entries): iterations, final relative residual and the member's completion time
+ * from the launch [ms]; statuses (may be NULL): each member's status as pressure_solve returns
+ * it.  Returns MG_OK if every member converged, else the first member's non-OK status. */
+mg_status mg_ensemble_solve(mg_ensemble* e, mg_solve_info* infos, int32_t* statuses, void* stream);
+
+void mg_ensemble_destroy(mg_ensemble* e);
+
 /* [yu; yp] = A [u; p], the mixed operator (needs mixed data). */
 mg_status mixed_apply(mg_handle* h, const double* u, const double* p, double* yu, double* yp,
                       void* stream);

@@ -83,6 +83,9 @@ _SIGS = {
     "mg_set_pressure_solver": [_VP, ctypes.POINTER(_PSolver)],
     "helmholtz_solve": [_VP, _DP, _DP, ctypes.POINTER(ctypes.c_double), _VP],
     "mg_inner_stats": [_VP, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_double)],
+    "mg_ensemble_create": [_VP, _I32, _VP, _VP, _D, ctypes.POINTER(ctypes.c_void_p)],
+    "mg_ensemble_solve": [_VP, ctypes.POINTER(_Info), ctypes.POINTER(ctypes.c_int32), _VP],
+    "mg_ensemble_destroy": [_VP],
     "mg_destroy": [_VP],
     "mg_sizes": [_VP, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)],
     "helmholtz_apply": [_VP, _DP, _DP, _VP],
@@ -123,7 +126,7 @@ def load() -> ctypes.CDLL:
         for name, args in _SIGS.items():
             fn = getattr(lib, name)
             fn.argtypes = args
-            fn.restype = None if name == "mg_destroy" else ctypes.c_int
+            fn.restype = None if name in ("mg_destroy", "mg_ensemble_destroy") else ctypes.c_int
         lib.mg_status_string.argtypes = [ctypes.c_int]
         lib.mg_status_string.restype = ctypes.c_char_p
         _lib = lib
@@ -396,6 +399,44 @@ def ensemble_pressure_solve(handles, bs, xs, tol: float = 1e-8, stream=None) -> 
     if st not in (MG_OK, MG_ERR_NOT_CONVERGED, MG_ERR_BREAKDOWN):
         raise MGError(st, "ensemble_pressure_solve")
     return [SolveInfo(sts[i], infos[i].iters, infos[i].rel_res, infos[i].ms) for i in range(n)]
+
+
+class Ensemble:
+    """An mg_ensemble: every member's pressure solve recorded into one CUDA graph (see
+    mg_ensemble_create in mgsolve.h).  The b and x tensors are bound at creation; solve() runs
+    all members with one graph launch and returns each member's SolveInfo."""
+
+    def __init__(self, handles, bs, xs, tol: float = 1e-8):
+        n = len(handles)
+        if n < 1 or len(bs) != n or len(xs) != n:
+            raise ValueError("one b and one x per handle, at least one member")
+        self.handles, self.bs, self.xs = list(handles), list(bs), list(xs)   # keep them alive
+        hs = (ctypes.c_void_p * n)(*[h.ptr for h in handles])
+        bp = (ctypes.c_void_p * n)(*[_ptr(h, b, h.ncell, "b").value for b, h in zip(bs, handles)])
+        xp = (ctypes.c_void_p * n)(*[_ptr(h, x, h.ncell, "x").value for x, h in zip(xs, handles)])
+        out = ctypes.c_void_p()
+        _check(load().mg_ensemble_create(hs, n, bp, xp, tol, ctypes.byref(out)), "mg_ensemble_create")
+        self._ptr = out
+
+    def solve(self, stream=None) -> list[SolveInfo]:
+        n = len(self.handles)
+        infos = (_Info * n)()
+        sts = (ctypes.c_int32 * n)()
+        st = load().mg_ensemble_solve(self._ptr, infos, sts, _stream(stream))
+        if st not in (MG_OK, MG_ERR_NOT_CONVERGED, MG_ERR_BREAKDOWN):
+            raise MGError(st, "mg_ensemble_solve")
+        return [SolveInfo(sts[i], infos[i].iters, infos[i].rel_res, infos[i].ms) for i in range(n)]
+
+    def destroy(self):
+        if self._ptr:
+            load().mg_ensemble_destroy(self._ptr)
+            self._ptr = ctypes.c_void_p(None)
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
 
 
 def mixed_solve(h: Handle, rhs_u, rhs_p, u, p, tol: float = 1e-8, stream=None) -> SolveInfo:

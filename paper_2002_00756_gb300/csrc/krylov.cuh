@@ -324,6 +324,67 @@ __global__ void __launch_bounds__(RED_THREADS) k_bicg_xr(size_t n, double* x, do
     }
 }
 
+// ---- one graph launch for an ensemble of pressure solves ----
+// Every member's GCR iterations run inside a conditional WHILE node of one CUDA graph; within
+// it, an IF node per restart slot j holds the V-cycle, the fused apply and the orthogonalisation
+// of slot j, and a second IF node the solution update that closes a restart cycle.  The
+// decisions the host takes after each iteration of a single solve (converged, breakdown,
+// iteration limit, end of a restart cycle) are taken here by one thread, in the same order
+// and FP64 arithmetic, by setting the conditions of those nodes.
+struct EnsState {
+    double bb;     // <b, b>
+    double rel;    // ||r|| / ||b|| after the last iteration
+    int it;        // iterations done
+    int status;    // MG_OK, MG_ERR_NOT_CONVERGED or MG_ERR_BREAKDOWN
+};
+
+struct EnsHandles {
+    cudaGraphConditionalHandle w;          // WHILE: another iteration
+    cudaGraphConditionalHandle c[MAXR];    // IF: iteration of slot j
+    cudaGraphConditionalHandle x[MAXR];    // IF: solution update after slot j
+};
+
+__device__ void ens_set_slots(const EnsHandles& hs, int R, int next, bool go) {
+    for (int k = 0; k < R; ++k) {
+        cudaGraphSetConditional(hs.c[k], (go && k == next) ? 1u : 0u);
+        cudaGraphSetConditional(hs.x[k], 0u);
+    }
+}
+
+// after <b, b>: start iterating unless b = 0, <b, b> is not finite or no iteration is allowed
+__global__ void k_ens_init(const GcrScal* S, EnsState* st, int R, int max_iter, EnsHandles hs) {
+    const double bb = S->bb;
+    const bool bad = !isfinite(bb);
+    const bool go = !bad && bb > 0.0 && max_iter > 0;
+    st->bb = bb;
+    st->it = 0;
+    st->rel = (!bad && bb > 0.0) ? 1.0 : 0.0;
+    st->status = bad ? MG_ERR_BREAKDOWN : (go ? MG_ERR_NOT_CONVERGED : MG_OK);
+    ens_set_slots(hs, R, 0, go);
+    cudaGraphSetConditional(hs.w, go ? 1u : 0u);
+}
+
+// after the iteration of slot j: the convergence test and the solution update of a single solve
+__global__ void k_ens_decide(const GcrScal* S, EnsState* st, int j, int R, int max_iter, double tol, EnsHandles hs) {
+    const int it = st->it + 1;
+    st->it = it;
+    const double rr = S->rr;
+    if (!isfinite(rr)) {   // breakdown: stop without the update (x keeps the last cycle's value)
+        st->status = MG_ERR_BREAKDOWN;
+        ens_set_slots(hs, R, 0, false);
+        cudaGraphSetConditional(hs.w, 0u);
+        return;
+    }
+    const double rel = sqrt(rr / st->bb);
+    st->rel = rel;
+    const bool done = rel <= tol;
+    if (done) st->status = MG_OK;
+    const bool go = !done && it < max_iter;
+    ens_set_slots(hs, R, j + 1 < R ? j + 1 : 0, go);
+    cudaGraphSetConditional(hs.x[j], (j == R - 1 || done || it == max_iter) ? 1u : 0u);
+    cudaGraphSetConditional(hs.w, go ? 1u : 0u);
+}
+
 // GCR step coefficients for direction J (classical Gram-Schmidt, one pass):
 //   beta_i = <w, w_i> / <w_i, w_i>,  <w', w'> = <w, w> - sum_i beta_i <w, w_i>,
 //   alpha = <r, w'> / <w', w'> with <r, w'> = <r, w> (the GCR residual is orthogonal to

@@ -1375,6 +1375,137 @@ void free_handle(mg_handle* h) {
 
 }  // namespace
 
+// ---- an ensemble of pressure solves as one CUDA graph ----
+struct mg_ensemble {
+    int device = 0;
+    int count = 0;
+    std::vector<mg_handle*> hs;
+    cudaStream_t cs = nullptr;            // capture stream
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    mg::EnsState* st = nullptr;           // device, one per member
+    mg::EnsState* host_st = nullptr;      // pinned copy, written by the graph's last node
+    cudaEvent_t ev_start = nullptr;
+    std::vector<cudaEvent_t> ev_end;      // per member, recorded by the graph
+};
+
+namespace {
+
+void free_ensemble(mg_ensemble* e) {
+    if (!e) return;
+    if (e->exec) cudaGraphExecDestroy(e->exec);
+    if (e->graph) cudaGraphDestroy(e->graph);
+    if (e->st) cudaFree(e->st);
+    if (e->host_st) cudaFreeHost(e->host_st);
+    if (e->ev_start) cudaEventDestroy(e->ev_start);
+    for (cudaEvent_t ev : e->ev_end)
+        if (ev) cudaEventDestroy(ev);
+    if (e->cs) cudaStreamDestroy(e->cs);
+    delete e;
+}
+
+// Ends the capture on e->cs and returns the nodes the next work depends on.
+mg_status end_segment(mg_ensemble* e, std::vector<cudaGraphNode_t>& deps) {
+    cudaStreamCaptureStatus cst;
+    const cudaGraphNode_t* d = nullptr;
+    size_t nd = 0;
+    CK(cudaStreamGetCaptureInfo(e->cs, &cst, nullptr, nullptr, &d, nullptr, &nd));
+    deps.assign(d, d + nd);
+    cudaGraph_t g = nullptr;
+    CK(cudaStreamEndCapture(e->cs, &g));
+    return MG_OK;
+}
+
+mg_status add_conditional(cudaGraph_t g, const std::vector<cudaGraphNode_t>& deps, cudaGraphConditionalHandle hnd,
+                          cudaGraphConditionalNodeType type, cudaGraphNode_t* node, cudaGraph_t* body) {
+    cudaGraphNodeParams p{};
+    p.type = cudaGraphNodeTypeConditional;
+    p.conditional.handle = hnd;
+    p.conditional.type = type;
+    p.conditional.size = 1;
+    CK(cudaGraphAddNode(node, g, deps.empty() ? nullptr : deps.data(), nullptr, deps.size(), &p));
+    *body = p.conditional.phGraph_out[0];
+    return MG_OK;
+}
+
+// The launches of one member: start, then WHILE { IF slot 0 {iteration}, IF {update}, ..., IF slot R-1
+// {iteration}, IF {update} }, then the member's end event.
+mg_status build_member(mg_ensemble* e, int i, mg_handle* h, const double* b, double* x, double tol,
+                       std::vector<cudaGraphNode_t>& ends) {
+    const int R = h->prm.gcr_restart;
+    const size_t n = cells(h, 0);
+    const cudaStreamCaptureMode mode = cudaStreamCaptureModeThreadLocal;
+    mg::EnsHandles hs{};
+    CK(cudaGraphConditionalHandleCreate(&hs.w, e->graph, 0, cudaGraphCondAssignDefault));
+    for (int j = 0; j < R; ++j) {
+        CK(cudaGraphConditionalHandleCreate(&hs.c[j], e->graph, 0, cudaGraphCondAssignDefault));
+        CK(cudaGraphConditionalHandleCreate(&hs.x[j], e->graph, 0, cudaGraphCondAssignDefault));
+    }
+    mg::EnsState* st = e->st + i;
+    // start: r = b, x = 0, <b, b>, first decision
+    std::vector<cudaGraphNode_t> deps;
+    CK(cudaStreamBeginCaptureToGraph(e->cs, e->graph, nullptr, nullptr, 0, mode));
+    CK(cudaMemcpyAsync(h->r, b, n * sizeof(double), cudaMemcpyDeviceToDevice, e->cs));
+    CK(cudaMemsetAsync(x, 0, n * sizeof(double), e->cs));
+    mg::k_dot<<<h->red_grid, mg::RED_THREADS, 0, e->cs>>>(n, b, b, h->partials, h->tickets + TK_DOT, &h->gs->bb);
+    mg::k_ens_init<<<1, 1, 0, e->cs>>>(h->gs, st, R, h->prm.max_iter, hs);
+    CK(cudaGetLastError());
+    TRY(end_segment(e, deps));
+    cudaGraphNode_t wnode;
+    cudaGraph_t wbody;
+    TRY(add_conditional(e->graph, deps, hs.w, cudaGraphCondTypeWhile, &wnode, &wbody));
+    std::vector<cudaGraphNode_t> prev;
+    for (int j = 0; j < R; ++j) {
+        cudaGraphNode_t inode, xnode;
+        cudaGraph_t ibody, xbody;
+        TRY(add_conditional(wbody, prev, hs.c[j], cudaGraphCondTypeIf, &inode, &ibody));
+        CK(cudaStreamBeginCaptureToGraph(e->cs, ibody, nullptr, nullptr, 0, mode));
+        double* z = h->Z + (size_t)j * h->glen;
+        double* w = h->W + (size_t)j * h->glen;
+        TRY(run_vcycle(h, h->r, z, e->cs));
+        TRY(apply_gcr(h, z, w, j, e->cs));
+        TRY(dispatch_j<RunOrth>(j, h, n, e->cs));
+        mg::k_ens_decide<<<1, 1, 0, e->cs>>>(h->gs, st, j, R, h->prm.max_iter, tol, hs);
+        CK(cudaGetLastError());
+        TRY(end_segment(e, deps));
+        TRY(add_conditional(wbody, {inode}, hs.x[j], cudaGraphCondTypeIf, &xnode, &xbody));
+        CK(cudaStreamBeginCaptureToGraph(e->cs, xbody, nullptr, nullptr, 0, mode));
+        TRY(dispatch_j<RunXupd>(j, h, n, x, e->cs));
+        TRY(end_segment(e, deps));
+        prev.assign(1, xnode);
+    }
+    // the member's end
+    CK(cudaStreamBeginCaptureToGraph(e->cs, e->graph, &wnode, nullptr, 1, mode));
+    CK(cudaEventRecord(e->ev_end[i], e->cs));
+    TRY(end_segment(e, deps));
+    ends.insert(ends.end(), deps.begin(), deps.end());
+    return MG_OK;
+}
+
+mg_status build_ensemble(mg_ensemble* e, const double* const* b, double* const* x, double tol) {
+    CK(cudaStreamCreateWithFlags(&e->cs, cudaStreamNonBlocking));
+    CK(cudaEventCreate(&e->ev_start));
+    e->ev_end.assign(e->count, nullptr);
+    for (auto& ev : e->ev_end) CK(cudaEventCreate(&ev));
+    if (cudaMalloc(&e->st, e->count * sizeof(mg::EnsState)) != cudaSuccess ||
+        cudaMallocHost(&e->host_st, e->count * sizeof(mg::EnsState)) != cudaSuccess) {
+        cudaGetLastError();
+        return MG_ERR_NOMEM;
+    }
+    CK(cudaGraphCreate(&e->graph, 0));
+    std::vector<cudaGraphNode_t> ends;
+    for (int i = 0; i < e->count; ++i) TRY(build_member(e, i, e->hs[i], b[i], x[i], tol, ends));
+    // last node: every member's state to the host
+    CK(cudaStreamBeginCaptureToGraph(e->cs, e->graph, ends.data(), nullptr, ends.size(), cudaStreamCaptureModeThreadLocal));
+    CK(cudaMemcpyAsync(e->host_st, e->st, e->count * sizeof(mg::EnsState), cudaMemcpyDeviceToHost, e->cs));
+    std::vector<cudaGraphNode_t> deps;
+    TRY(end_segment(e, deps));
+    CK(cudaGraphInstantiate(&e->exec, e->graph, 0));
+    return MG_OK;
+}
+
+}  // namespace
+
 // =====================================================================================
 static mg_status mg_setup_check(const mg_mesh* mesh, const mg_params* prm, const double* g, const mg_mixed* mixed);
 
@@ -1661,6 +1792,69 @@ mg_status ensemble_pressure_solve(mg_handle* const* handles, int32_t count, cons
         if (st == MG_OK) st = g[i].st;
     }
     return st;
+}
+
+mg_status mg_ensemble_create(mg_handle* const* handles, int32_t count, const double* const* b, double* const* x,
+                             double tol, mg_ensemble** out) {
+    if (!out) return MG_ERR_ARG;
+    *out = nullptr;
+    if (count < 1 || !handles || !b || !x || !(tol >= 0.0)) return MG_ERR_ARG;
+    for (int i = 0; i < count; ++i) {
+        if (!handles[i] || !b[i] || !x[i] || b[i] == x[i] || handles[i]->device != handles[0]->device)
+            return MG_ERR_ARG;
+        for (int k = 0; k < i; ++k)
+            if (handles[k] == handles[i]) return MG_ERR_ARG;
+        if (handles[i]->prof || handles[i]->mixed) return MG_ERR_UNSUPPORTED;
+    }
+    DeviceGuard dg(handles[0]->device);
+    mg_ensemble* e = new (std::nothrow) mg_ensemble();
+    if (!e) return MG_ERR_NOMEM;
+    e->device = handles[0]->device;
+    e->count = count;
+    e->hs.assign(handles, handles + count);
+    const mg_status st = build_ensemble(e, b, x, tol);
+    if (st != MG_OK) {
+        cudaStreamCaptureStatus cst;
+        if (e->cs && cudaStreamIsCapturing(e->cs, &cst) == cudaSuccess && cst != cudaStreamCaptureStatusNone) {
+            cudaGraph_t g = nullptr;
+            cudaStreamEndCapture(e->cs, &g);
+        }
+        cudaGetLastError();
+        free_ensemble(e);
+        return st;
+    }
+    *out = e;
+    return MG_OK;
+}
+
+mg_status mg_ensemble_solve(mg_ensemble* e, mg_solve_info* infos, int32_t* statuses, void* stream) {
+    if (!e) return MG_ERR_ARG;
+    DeviceGuard dg(e->device);
+    cudaStream_t s = S(stream);
+    CK(cudaEventRecord(e->ev_start, s));
+    CK(cudaGraphLaunch(e->exec, s));
+    CK(cudaStreamSynchronize(s));
+    mg_status st = MG_OK;
+    for (int i = 0; i < e->count; ++i) {
+        const mg::EnsState& m = e->host_st[i];
+        if (infos) {
+            float ms = 0.f;
+            CK(cudaEventElapsedTime(&ms, e->ev_start, e->ev_end[i]));
+            infos[i].iters = m.it;
+            infos[i].rel_res = m.rel;
+            infos[i].ms = ms;
+        }
+        if (statuses) statuses[i] = m.status;
+        if (st == MG_OK) st = (mg_status)m.status;
+    }
+    return st;
+}
+
+void mg_ensemble_destroy(mg_ensemble* e) {
+    if (!e) return;
+    DeviceGuard dg(e->device);
+    cudaDeviceSynchronize();
+    free_ensemble(e);
 }
 
 mg_status mixed_solve(mg_handle* h, const double* rhs_u, const double* rhs_p, double* u, double* p, double tol,

@@ -66,3 +66,73 @@ def test_members_match_their_single_solves(mg):
         mg.ensemble_pressure_solve([hs[0], hs[0]], [bs[0], bs[0]], [xs[0], xs[0].clone()])   # a handle twice
     for h in hs:
         h.destroy()
+
+
+def test_one_graph_launch_matches_single_solves(mg):
+    """mg_ensemble: every member's whole solve in one CUDA graph (device-side convergence
+    decisions).  Each member gets what pressure_solve gives it alone, bit for bit, with the same
+    iteration count and status, including a zero right-hand side, a member stopped by its
+    iteration limit and a member whose right-hand side holds a NaN (breakdown)."""
+    hs, bs, xs = [], [], []
+    members = MEMBERS + [(syn.small_config(8, 12, levels=2, seed=syn.BASE_SEED + 35), "fp32", 200, 1.0)]
+    for cfg, prec, max_iter, scale in members:
+        inp = syn.make_inputs(cfg, mixed=False)
+        h = mg.mg_setup_config(cfg, inp, precision=prec, mixed=False, max_iter=max_iter)
+        b = torch.from_numpy(scale * inp["rhs"]).cuda()
+        hs.append(h)
+        bs.append(b)
+        xs.append(torch.full_like(b, float("nan")))
+    bs[-1][5] = float("nan")
+    ens = mg.Ensemble(hs, bs, xs, tol=1e-9)
+    for call in range(2):
+        if call == 1:   # new right-hand sides in the bound buffers
+            for i, b in enumerate(bs[:-1]):
+                b.mul_(-0.5).add_(0.25 * torch.from_numpy(syn.normal(60 + i, 0, b.numel())).cuda())
+        refs = []
+        for h, b in zip(hs, bs):
+            x = torch.full_like(b, float("nan"))
+            refs.append((x, mg.pressure_solve(h, b, x, tol=1e-9)))
+        infos = ens.solve()
+        torch.cuda.synchronize()
+        for i, ((xr, ir), x, info) in enumerate(zip(refs, xs, infos)):
+            assert info.status == ir.status and info.iters == ir.iters, (call, i, info, ir)
+            assert info.rel_res == ir.rel_res or (np.isnan(info.rel_res) and np.isnan(ir.rel_res)) or \
+                ir.status == mg.MG_ERR_BREAKDOWN
+            if ir.status != mg.MG_ERR_BREAKDOWN:
+                assert torch.equal(x, xr), (call, i)
+            assert info.ms > 0.0
+        assert infos[3].iters == 0 and infos[3].converged
+        assert infos[4].status == mg.MG_ERR_NOT_CONVERGED and infos[4].iters == 2
+        assert infos[-1].status == mg.MG_ERR_BREAKDOWN
+    ens.destroy()
+    for h in hs:
+        h.destroy()
+
+
+@pytest.mark.parametrize("one_launch", [False, True])
+def test_every_member_against_the_oracle_operator(mg, one_launch):
+    """Members of the benchmarked kind (C32 and larger, 30 / 50 / 70 levels, 4-level FP32
+    V-cycle) and small ones: every member's true residual under the oracle's operator."""
+    from oracle.problem import pressure_hierarchy
+    shapes = [(32, 30), (40, 50), (48, 70), (8, 30), (16, 50), (24, 70)]
+    hs, bs, xs, ops = [], [], [], []
+    for i, (n, nlev) in enumerate(shapes):
+        cfg = syn.small_config(n, nlev, levels=4 if n % 8 == 0 else 3, seed=syn.BASE_SEED + 300 + i)
+        inp = syn.make_inputs(cfg, mixed=False)
+        hs.append(mg.mg_setup_config(cfg, inp, precision="fp32", mixed=False))
+        bs.append(torch.from_numpy(inp["rhs"]).cuda())
+        xs.append(torch.zeros_like(bs[-1]))
+        ops.append((pressure_hierarchy(cfg, inp).levels[0], inp["rhs"]))
+    if one_launch:
+        ens = mg.Ensemble(hs, bs, xs, tol=1e-9)
+        infos = ens.solve()
+        ens.destroy()
+    else:
+        infos = mg.ensemble_pressure_solve(hs, bs, xs, tol=1e-9)
+    for (H, rhs), x, info, shp in zip(ops, xs, infos, shapes):
+        assert info.converged, (shp, info)
+        true = np.linalg.norm(rhs - H.apply(x.cpu().numpy()).ravel()) / np.linalg.norm(rhs)
+        print(f"member C{shp[0]}L{shp[1]}: {info.iters} iterations, true residual {true:.3e}")
+        assert true <= 1.05e-9, shp
+    for h in hs:
+        h.destroy()
