@@ -190,6 +190,11 @@ void mg_destroy(mg_handle* h);
 
 const char* mg_status_string(mg_status s);
 
+/* Name of the CUDA runtime error behind the last MG_ERR_CUDA returned on the calling thread
+ * (e.g. "cudaErrorMemoryAllocation"), or "no CUDA error".  A non-sticky error is cleared when it
+ * is reported, so it does not surface again in a later call. */
+const char* mg_last_cuda_error(void);
+
 /* Sizes of the handle's problem: ncol and N of the finest level, velocity unknowns
  * (0 without mixed data).  Any pointer may be NULL. */
 mg_status mg_sizes(const mg_handle* h, int64_t* ncol, int64_t* ncell, int64_t* nu);

@@ -27,7 +27,8 @@ PRECISIONS = {"fp64": MG_FP64, "fp32": MG_FP32, "fp32_bf16": MG_FP32_BF16COEF}
 class MGError(RuntimeError):
     def __init__(self, status: int, what: str):
         self.status = status
-        super().__init__(f"{what}: {status_string(status)} ({status})")
+        extra = f" [{load().mg_last_cuda_error().decode()}]" if status == MG_ERR_CUDA else ""
+        super().__init__(f"{what}: {status_string(status)} ({status}){extra}")
 
 
 class _Mesh(ctypes.Structure):
@@ -129,6 +130,8 @@ def load() -> ctypes.CDLL:
             fn.restype = None if name in ("mg_destroy", "mg_ensemble_destroy") else ctypes.c_int
         lib.mg_status_string.argtypes = [ctypes.c_int]
         lib.mg_status_string.restype = ctypes.c_char_p
+        lib.mg_last_cuda_error.argtypes = []
+        lib.mg_last_cuda_error.restype = ctypes.c_char_p
         _lib = lib
     return _lib
 

@@ -447,6 +447,228 @@ __global__ void __launch_bounds__(MG_SWEEP_BLOCK, 4) k_sweep(Lvl<T, C> L, const 
 }
 
 // ---------------------------------------------------------------------------------------
+// The same block-Jacobi sweep (same thread layout, same arithmetic in the same order, so the
+// same result bit for bit) for FP32 levels of an even number NLEV of levels, with the
+// elimination's stash (w_i, e_i) in registers instead of shared memory: every step of the
+// walk is unrolled (NS = NLEV / 2 steps per half), so the stash is NS register pairs.  The
+// shared memory the stash occupied holds instead a DEEP-slot ring that brings every value a
+// step reads -- the own column's b, next iterate and E / N / vertical faces, and the N, S (and,
+// at the ends of the lane group or across panel edges, E, W) neighbour iterates, the S and W
+// faces and the prolongation terms -- by asynchronous 4-byte copies, so no step issues a
+// global load: the walk waits only on its ring slot.
+template <int NLEV>
+struct SweepRsBlocks {   // resident blocks per SM: the stash of 70 levels needs the registers of 3
+    static constexpr int value = NLEV > 50 ? 3 : 4;
+};
+
+// SHN > 0: the neighbours' iterates and the S and W faces come instead through a register ring
+// loaded SHN steps ahead (plain and zero-start sweeps only).
+template <int NLEV, int MODE, typename B, typename O, bool BCOPY, int DEEP, int SHN = 0>
+__global__ void __launch_bounds__(MG_SWEEP_BLOCK, SweepRsBlocks<NLEV>::value)
+    k_sweep_rs(Lvl<float, float> L, const float* __restrict__ x, const float* __restrict__ xc, int ncol_c,
+               const B* __restrict__ b, float* __restrict__ bcopy, O* __restrict__ xo, float omega) {
+    static_assert(NLEV % 2 == 0 && NLEV >= 2, "even level count");
+    static_assert(SHN == 0 || !(MODE == XM_PROLONG || MODE == XM_PROLONG0), "register ring: no prolongation");
+    constexpr int NS = NLEV / 2;
+    constexpr bool PRO = (MODE == XM_PROLONG || MODE == XM_PROLONG0);
+    constexpr bool RAW = (MODE == XM_PLAIN || MODE == XM_PROLONG);
+    constexpr bool BD = sizeof(B) == 8;
+    // word slots of one ring entry (FP32): faces E, N, vertical ahead, S, W; iterates next, N, S,
+    // E, W; prolongation terms next, N, S, E, W; b when it is FP32
+    enum { W_TE, W_TN, W_TV, W_TS, W_TW, W_END0 };
+    constexpr int W_XN = W_END0, W_XNB = W_XN + 1, W_XS = W_XN + 2, W_XE = W_XN + 3, W_XW = W_XN + 4;
+    constexpr int W_END1 = RAW ? W_XN + 5 : W_END0;
+    constexpr int W_CN = W_END1, W_CNB = W_CN + 1, W_CS = W_CN + 2, W_CE = W_CN + 3, W_CW = W_CN + 4;
+    constexpr int W_END2 = PRO ? W_CN + 5 : W_END1;
+    constexpr int W_B = W_END2;
+    constexpr int NW = BD ? W_END2 : W_END2 + 1;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int tid = threadIdx.x, bd = blockDim.x;
+    double* rbd = reinterpret_cast<double*>(smem_raw);                        // [DEEP][bd] (FP64 b)
+    float* ring = reinterpret_cast<float*>(smem_raw + (BD ? (size_t)DEEP * bd * 8 : 0));   // [DEEP][NW][bd]
+    float* srdz = ring + (size_t)DEEP * NW * bd;                              // [NLEV]
+    for (int k = tid; k < NLEV; k += bd) srdz[k] = __ldg(L.rdz + k);
+    __syncthreads();
+    const int lane = tid & 31;
+    const int nwh = bd >> 6;
+    const bool upper = (tid >> 5) >= nwh;
+    const int c_raw = blockIdx.x * (bd >> 1) + ((tid >> 5) - (upper ? nwh : 0)) * 32 + lane;
+    const bool active = c_raw < L.ncol;
+    const int c = active ? c_raw : L.ncol - 1;
+    const int dir = upper ? -1 : 1;
+    const int kfirst = upper ? NLEV - 1 : 0;
+    const unsigned ncol = L.ncol;
+    const unsigned kc0 = (unsigned)kfirst * ncol, kcc0 = (unsigned)kfirst * (unsigned)ncol_c;
+    const unsigned dkc = upper ? 0u - ncol : ncol, dkcc = upper ? 0u - (unsigned)ncol_c : (unsigned)ncol_c;
+    int nb[4], fo[4], pn[4] = {0, 0, 0, 0}, pc = 0;
+#pragma unroll
+    for (int s = 0; s < 4; ++s) {
+        nb[s] = __ldg(L.nbr + s * ncol + c);
+        fo[s] = __ldg(L.fof + s * ncol + c);
+    }
+    if (PRO) {
+        pc = parent_col(c, L.n);
+#pragma unroll
+        for (int s = 0; s < 4; ++s) pn[s] = parent_col(nb[s], L.n);
+    }
+    const float rA = __ldg(L.rA + c);
+    const bool shE = lane != 31 && nb[0] == c + 1;
+    const bool shW = lane != 0 && nb[1] == c - 1;
+    const bool shWf = shW && fo[1] == __ldg(L.fof + (c > 0 ? c - 1 : 0));
+    const unsigned tvo = (unsigned)c + (upper ? 0u : ncol);   // the vertical face ahead of the walk
+    auto slot = [&](int j, int w) -> float* { return ring + ((size_t)j * NW + w) * bd + tid; };
+    auto stage = [&](int i) {
+        const int j = i % DEEP;
+        const unsigned kc = kc0 + (unsigned)i * dkc, kcc = kcc0 + (unsigned)i * dkcc;
+        if (BD) __pipeline_memcpy_async(rbd + (size_t)j * bd + tid, b + (kc + c), 8);
+        else __pipeline_memcpy_async(slot(j, W_B), b + (kc + c), 4);
+        __pipeline_memcpy_async(slot(j, W_TE), L.Th + (2 * kc + fo[0]), 4);
+        __pipeline_memcpy_async(slot(j, W_TN), L.Th + (2 * kc + fo[2]), 4);
+        __pipeline_memcpy_async(slot(j, W_TV), L.Tv + (kc + tvo), 4);
+        if (SHN == 0) {
+            __pipeline_memcpy_async(slot(j, W_TS), L.Th + (2 * kc + fo[3]), 4);
+            if (!shWf) __pipeline_memcpy_async(slot(j, W_TW), L.Th + (2 * kc + fo[1]), 4);
+        }
+        if (RAW) {
+            __pipeline_memcpy_async(slot(j, W_XN), x + (kc + dkc + c), 4);
+            if (SHN == 0) {
+                __pipeline_memcpy_async(slot(j, W_XNB), x + (kc + nb[2]), 4);
+                __pipeline_memcpy_async(slot(j, W_XS), x + (kc + nb[3]), 4);
+                if (!shE) __pipeline_memcpy_async(slot(j, W_XE), x + (kc + nb[0]), 4);
+                if (!shW) __pipeline_memcpy_async(slot(j, W_XW), x + (kc + nb[1]), 4);
+            }
+        }
+        if (PRO) {
+            __pipeline_memcpy_async(slot(j, W_CN), xc + (kcc + dkcc + pc), 4);
+            __pipeline_memcpy_async(slot(j, W_CNB), xc + (kcc + pn[2]), 4);
+            __pipeline_memcpy_async(slot(j, W_CS), xc + (kcc + pn[3]), 4);
+            if (!shE) __pipeline_memcpy_async(slot(j, W_CE), xc + (kcc + pn[0]), 4);
+            if (!shW) __pipeline_memcpy_async(slot(j, W_CW), xc + (kcc + pn[1]), 4);
+        }
+    };
+#pragma unroll
+    for (int i = 0; i < DEEP; ++i) {
+        if (i < NS) stage(i);
+        __pipeline_commit();
+    }
+    // register ring of the neighbour values (SHN > 0): iterates E, W, N, S and faces S, W
+    struct Nb {
+        float xh[4], ts, tw;
+    };
+    constexpr int SR = SHN > 0 ? SHN : 1;
+    Nb nr[SR];
+    auto load_nb = [&](int i, Nb& d) {
+        const unsigned kc = kc0 + (unsigned)i * dkc;
+        if (RAW) {
+            if (!shE) d.xh[0] = __ldg(x + (kc + nb[0]));
+            if (!shW) d.xh[1] = __ldg(x + (kc + nb[1]));
+            d.xh[2] = __ldg(x + (kc + nb[2]));
+            d.xh[3] = __ldg(x + (kc + nb[3]));
+        }
+        d.ts = __ldg(L.Th + (2 * kc + fo[3]));
+        if (!shWf) d.tw = __ldg(L.Th + (2 * kc + fo[1]));
+    };
+    if (SHN > 0) {
+#pragma unroll
+        for (int i = 0; i < SR; ++i)
+            if (i < NS) load_nb(i, nr[i]);
+    }
+    float xprev = 0.f, x0 = 0.f, tprev = 0.f;
+    if (RAW) x0 = __ldg(x + kc0 + c);
+    if (PRO) x0 += __ldg(xc + kcc0 + pc);
+    float q = 0.f, ip = 0.f, y = 0.f, anext = 0.f;
+    float sw[NS], se[NS];
+#pragma unroll
+    for (int i = 0; i < NS; ++i) {
+        const int j = i % DEEP;
+        __pipeline_wait_prior(DEEP - 1);
+        __syncwarp();   // every lane's copies of this slot are complete and visible
+        const float bk = BD ? (float)rbd[(size_t)j * bd + tid] : *slot(j, W_B);
+        const float te = *slot(j, W_TE), tn = *slot(j, W_TN), tv = *slot(j, W_TV);
+        float ts, tw, xn = 0.f, xh[4] = {0.f, 0.f, 0.f, 0.f};
+        if (SHN > 0) {
+            const Nb e = nr[i % SR];
+            if (i + SR < NS) load_nb(i + SR, nr[i % SR]);
+            ts = e.ts;
+            tw = shWf ? ring[((size_t)j * NW + W_TE) * bd + tid - 1] : e.tw;
+            if (RAW) {
+#pragma unroll
+                for (int q2 = 0; q2 < 4; ++q2) xh[q2] = e.xh[q2];
+            }
+        } else {
+            ts = *slot(j, W_TS);
+            tw = shWf ? ring[((size_t)j * NW + W_TE) * bd + tid - 1] : *slot(j, W_TW);
+            if (RAW) {
+                xh[0] = *slot(j, W_XE);
+                xh[1] = *slot(j, W_XW);
+                xh[2] = *slot(j, W_XNB);
+                xh[3] = *slot(j, W_XS);
+            }
+        }
+        if (RAW) xn = *slot(j, W_XN);
+        if (PRO) {
+            xn += *slot(j, W_CN);
+            xh[0] += *slot(j, W_CE);
+            xh[1] += *slot(j, W_CW);
+            xh[2] += *slot(j, W_CNB);
+            xh[3] += *slot(j, W_CS);
+        }
+        __syncwarp();   // reads of the slot are done before it is refilled
+        if (i + DEEP < NS) stage(i + DEEP);
+        __pipeline_commit();
+        const float xEl = __shfl_down_sync(0xffffffffu, x0, 1);
+        const float xWl = __shfl_up_sync(0xffffffffu, x0, 1);
+        if (shE) xh[0] = xEl;
+        if (shW) xh[1] = xWl;
+        const float rdz = srdz[kfirst + dir * i];
+        if (BCOPY) bcopy[kc0 + (unsigned)i * dkc + c] = bk;
+        float r = bk;
+        if (MODE != XM_ZERO) {
+            float hx = te * (x0 - xh[0]);
+            hx += tw * (x0 - xh[1]);
+            hx += tn * (x0 - xh[2]);
+            hx += ts * (x0 - xh[3]);
+            r -= x0 + (rA * hx + rdz * (tv * (x0 - xn) + tprev * (x0 - xprev)));
+        }
+        anext = rdz * tv;
+        const float m = (rdz * tprev) * ip;
+        q = (1.f + rA * ((te + tw) + (tn + ts))) + m * q;
+        const float p = q + anext;
+        y = r + m * y;
+        ip = 1.f / p;
+        const float ei = anext * ip;
+        sw[i] = x0 + omega * (y * ip) - ei * xn;
+        se[i] = ei;
+        xprev = x0;
+        x0 = xn;
+        tprev = tv;
+    }
+    __pipeline_wait_prior(0);
+    // interface rows: through shared memory from the thread tid ^ (bd / 2) holding the other half
+    __syncthreads();
+    float* xch = reinterpret_cast<float*>(smem_raw);
+    xch[tid] = q;
+    xch[bd + tid] = y;
+    xch[2 * bd + tid] = anext;
+    __syncthreads();
+    const int pt = tid ^ (bd >> 1);
+    const float qo = xch[pt], yo = xch[bd + pt], ao = xch[2 * bd + pt];
+    const float po = qo + ao;
+    const float dlt = (y * po + anext * yo) / (q * po + anext * qo);
+    if (!active) return;
+    float out = xprev + omega * dlt;
+    O* pout = xo + c;
+    unsigned ko = kc0 + (unsigned)(NS - 1) * dkc;
+    pout[ko] = (O)out;
+#pragma unroll
+    for (int i = NS - 2; i >= 0; --i) {
+        out = sw[i] + se[i] * out;
+        ko -= dkc;
+        pout[ko] = (O)out;
+    }
+}
+
+// ---------------------------------------------------------------------------------------
 // Residual and restriction (Algorithm 1): bc[k][C] = sum_q w[q][C] (b - H x)[k][child_q],
 // w = area_child / area_C; one thread per coarse column and chunk of kchunk levels (there is
 // no vertical recurrence, so short chunks give many independent threads).

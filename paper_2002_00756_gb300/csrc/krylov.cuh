@@ -344,6 +344,13 @@ struct EnsHandles {
     cudaGraphConditionalHandle x[MAXR];    // IF: solution update after slot j
 };
 
+// the device's global nanosecond clock
+__global__ void k_stamp(unsigned long long* out) {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    *out = t;
+}
+
 __device__ void ens_set_slots(const EnsHandles& hs, int R, int next, bool go) {
     for (int k = 0; k < R; ++k) {
         cudaGraphSetConditional(hs.c[k], (go && k == next) ? 1u : 0u);

@@ -176,10 +176,19 @@ enum { TK_DOT = 0, TK_SUMS, TK_ORTH, TK_BICG, TK_COUNT };
 // many independent threads, so the loads of different threads overlap
 constexpr int APPLY_KCHUNK = 8;
 
-#define CK(call)                                   \
-    do {                                           \
-        cudaError_t e_ = (call);                   \
-        if (e_ != cudaSuccess) return MG_ERR_CUDA; \
+// the CUDA error behind the last MG_ERR_CUDA of this thread (mg_last_cuda_error)
+thread_local cudaError_t g_last_cuda = cudaSuccess;
+
+// A failed runtime call returns MG_ERR_CUDA; a non-sticky error is cleared so that it does not
+// surface again in a later, unrelated call.
+#define CK(call)                       \
+    do {                               \
+        cudaError_t e_ = (call);       \
+        if (e_ != cudaSuccess) {       \
+            g_last_cuda = e_;          \
+            cudaGetLastError();        \
+            return MG_ERR_CUDA;        \
+        }                              \
     } while (0)
 
 template <typename P>
@@ -317,6 +326,41 @@ struct SweepPF {
     static constexpr int shal = sizeof(T) == 8 ? 2 : MG_SWEEP_SHAL32;
 };
 
+// FP32 levels of 30, 50 or 70 levels use the register-stash sweep (k_sweep_rs) where it was
+// measured faster at C192L70: every sweep from a zero iterate (the first of each level; finest
+// level 107 us against 110, levels 1-3 27 / 14 / 11 us against 36 / 20 / 19), and the plain
+// sweeps of levels of at most MG_SWEEP_RS_PLAIN_NCOL columns (the coarsest, 13 us against 15).
+// On larger levels its eleven staged words per step make the plain sweep slower (167 us against
+// 121 on the finest level), and the sweep with fused prolongation slower on every level.
+#ifndef MG_SWEEP_REG
+#define MG_SWEEP_REG 1
+#endif
+#ifndef MG_SWEEP_RS_PLAIN_NCOL
+#define MG_SWEEP_RS_PLAIN_NCOL 4000
+#endif
+
+// The register-stash sweep (k_sweep_rs) for an FP32 level of NLEV levels, bd threads per block
+#ifndef MG_SWEEP_RS_SHN
+#define MG_SWEEP_RS_SHN 0    // > 0: the register-stash sweep loads neighbour values into a register ring
+#endif
+
+template <int NLEV, int MODE, typename B, typename O, bool BCOPY>
+mg_status launch_sweep_rs(const Lvl<float, float>& L, const float* x, const float* xc, int ncol_c, const B* b,
+                          float* bcopy, O* xo, float omega, int bd, cudaStream_t s) {
+    constexpr bool PRO = (MODE == mg::XM_PROLONG || MODE == mg::XM_PROLONG0);
+    constexpr bool RAW = (MODE == mg::XM_PLAIN || MODE == mg::XM_PROLONG);
+    // ring depth: the shared memory of the resident blocks (3 at 70 levels, else 4)
+    constexpr int DEEP = mg::SweepRsBlocks<NLEV>::value == 3 ? ((PRO && RAW) ? 8 : 12) : ((PRO && RAW) ? 6 : 8);
+    constexpr int NW = 5 + (RAW ? 5 : 0) + (PRO ? 5 : 0) + (sizeof(B) == 8 ? 0 : 1);
+    const size_t smem = (size_t)DEEP * bd * (sizeof(B) == 8 ? 8 : 0) + (size_t)DEEP * NW * bd * 4 + NLEV * 4;
+    auto kern = mg::k_sweep_rs<NLEV, MODE, B, O, BCOPY, DEEP, PRO ? 0 : MG_SWEEP_RS_SHN>;
+    if (smem > 48 * 1024) CK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    const int grid = (L.ncol + bd / 2 - 1) / (bd / 2);
+    kern<<<grid, bd, smem, s>>>(L, x, xc, ncol_c, b, bcopy, xo, omega);
+    CK(cudaGetLastError());
+    return MG_OK;
+}
+
 template <typename T, typename C, int MODE, typename X, typename B, typename O, bool BCOPY>
 mg_status launch_sweep(mg_handle* h, int lev, const Lvl<T, C>& L, const X* x, const T* xc, int ncol_c,
                        const B* b, T* bcopy, O* xo, double omega, cudaStream_t s) {
@@ -326,6 +370,17 @@ mg_status launch_sweep(mg_handle* h, int lev, const Lvl<T, C>& L, const X* x, co
     if (MODE == mg::XM_PROLONG || MODE == mg::XM_PROLONG0) per += 0.25 * sizeof(T);
     if (BCOPY) per += sizeof(T);
     Prof pr(h, MG_K_SWEEP, lev, nc * per, s, MODE);
+    if constexpr (MG_SWEEP_REG && std::is_same<T, float>::value && std::is_same<C, float>::value &&
+                  std::is_same<X, float>::value && (MODE == mg::XM_ZERO || MODE == mg::XM_PLAIN)) {
+        const int bdr = (h && h->lv[lev].sweep_bd > 0) ? h->lv[lev].sweep_bd : MG_SWEEP_BLOCK;
+        const bool use = MODE == mg::XM_ZERO || L.ncol <= MG_SWEEP_RS_PLAIN_NCOL;
+        if (use) switch (L.nlev) {
+            case 70: return launch_sweep_rs<70, MODE, B, O, BCOPY>(L, x, xc, ncol_c, b, bcopy, xo, (float)omega, bdr, s);
+            case 50: return launch_sweep_rs<50, MODE, B, O, BCOPY>(L, x, xc, ncol_c, b, bcopy, xo, (float)omega, bdr, s);
+            case 30: return launch_sweep_rs<30, MODE, B, O, BCOPY>(L, x, xc, ncol_c, b, bcopy, xo, (float)omega, bdr, s);
+            default: break;
+        }
+    }
     // two threads per column; per thread the shared memory holds the asynchronous-copy
     // ring (DEEP slots of b, the next iterate and, unless BF16, three coefficients) and the
     // stash (2 values per step of half a column); it must fit the budget
@@ -1385,8 +1440,8 @@ struct mg_ensemble {
     cudaGraphExec_t exec = nullptr;
     mg::EnsState* st = nullptr;           // device, one per member
     mg::EnsState* host_st = nullptr;      // pinned copy, written by the graph's last node
-    cudaEvent_t ev_start = nullptr;
-    std::vector<cudaEvent_t> ev_end;      // per member, recorded by the graph
+    unsigned long long* stamps = nullptr; // device: launch time, then every member's end [ns]
+    unsigned long long* host_stamps = nullptr;
 };
 
 namespace {
@@ -1397,9 +1452,8 @@ void free_ensemble(mg_ensemble* e) {
     if (e->graph) cudaGraphDestroy(e->graph);
     if (e->st) cudaFree(e->st);
     if (e->host_st) cudaFreeHost(e->host_st);
-    if (e->ev_start) cudaEventDestroy(e->ev_start);
-    for (cudaEvent_t ev : e->ev_end)
-        if (ev) cudaEventDestroy(ev);
+    if (e->stamps) cudaFree(e->stamps);
+    if (e->host_stamps) cudaFreeHost(e->host_stamps);
     if (e->cs) cudaStreamDestroy(e->cs);
     delete e;
 }
@@ -1431,7 +1485,7 @@ mg_status add_conditional(cudaGraph_t g, const std::vector<cudaGraphNode_t>& dep
 // The launches of one member: start, then WHILE { IF slot 0 {iteration}, IF {update}, ..., IF slot R-1
 // {iteration}, IF {update} }, then the member's end event.
 mg_status build_member(mg_ensemble* e, int i, mg_handle* h, const double* b, double* x, double tol,
-                       std::vector<cudaGraphNode_t>& ends) {
+                       const std::vector<cudaGraphNode_t>& root, std::vector<cudaGraphNode_t>& ends) {
     const int R = h->prm.gcr_restart;
     const size_t n = cells(h, 0);
     const cudaStreamCaptureMode mode = cudaStreamCaptureModeThreadLocal;
@@ -1444,7 +1498,7 @@ mg_status build_member(mg_ensemble* e, int i, mg_handle* h, const double* b, dou
     mg::EnsState* st = e->st + i;
     // start: r = b, x = 0, <b, b>, first decision
     std::vector<cudaGraphNode_t> deps;
-    CK(cudaStreamBeginCaptureToGraph(e->cs, e->graph, nullptr, nullptr, 0, mode));
+    CK(cudaStreamBeginCaptureToGraph(e->cs, e->graph, root.data(), nullptr, root.size(), mode));
     CK(cudaMemcpyAsync(h->r, b, n * sizeof(double), cudaMemcpyDeviceToDevice, e->cs));
     CK(cudaMemsetAsync(x, 0, n * sizeof(double), e->cs));
     mg::k_dot<<<h->red_grid, mg::RED_THREADS, 0, e->cs>>>(n, b, b, h->partials, h->tickets + TK_DOT, &h->gs->bb);
@@ -1476,7 +1530,8 @@ mg_status build_member(mg_ensemble* e, int i, mg_handle* h, const double* b, dou
     }
     // the member's end
     CK(cudaStreamBeginCaptureToGraph(e->cs, e->graph, &wnode, nullptr, 1, mode));
-    CK(cudaEventRecord(e->ev_end[i], e->cs));
+    mg::k_stamp<<<1, 1, 0, e->cs>>>(e->stamps + 1 + i);
+    CK(cudaGetLastError());
     TRY(end_segment(e, deps));
     ends.insert(ends.end(), deps.begin(), deps.end());
     return MG_OK;
@@ -1484,21 +1539,27 @@ mg_status build_member(mg_ensemble* e, int i, mg_handle* h, const double* b, dou
 
 mg_status build_ensemble(mg_ensemble* e, const double* const* b, double* const* x, double tol) {
     CK(cudaStreamCreateWithFlags(&e->cs, cudaStreamNonBlocking));
-    CK(cudaEventCreate(&e->ev_start));
-    e->ev_end.assign(e->count, nullptr);
-    for (auto& ev : e->ev_end) CK(cudaEventCreate(&ev));
     if (cudaMalloc(&e->st, e->count * sizeof(mg::EnsState)) != cudaSuccess ||
-        cudaMallocHost(&e->host_st, e->count * sizeof(mg::EnsState)) != cudaSuccess) {
+        cudaMallocHost(&e->host_st, e->count * sizeof(mg::EnsState)) != cudaSuccess ||
+        cudaMalloc(&e->stamps, (e->count + 1) * sizeof(unsigned long long)) != cudaSuccess ||
+        cudaMallocHost(&e->host_stamps, (e->count + 1) * sizeof(unsigned long long)) != cudaSuccess) {
         cudaGetLastError();
         return MG_ERR_NOMEM;
     }
     CK(cudaGraphCreate(&e->graph, 0));
+    // root: the launch time; every member starts after it
+    std::vector<cudaGraphNode_t> root, deps;
+    CK(cudaStreamBeginCaptureToGraph(e->cs, e->graph, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+    mg::k_stamp<<<1, 1, 0, e->cs>>>(e->stamps);
+    CK(cudaGetLastError());
+    TRY(end_segment(e, root));
     std::vector<cudaGraphNode_t> ends;
-    for (int i = 0; i < e->count; ++i) TRY(build_member(e, i, e->hs[i], b[i], x[i], tol, ends));
-    // last node: every member's state to the host
+    for (int i = 0; i < e->count; ++i) TRY(build_member(e, i, e->hs[i], b[i], x[i], tol, root, ends));
+    // last nodes: every member's state and time stamp to the host
     CK(cudaStreamBeginCaptureToGraph(e->cs, e->graph, ends.data(), nullptr, ends.size(), cudaStreamCaptureModeThreadLocal));
     CK(cudaMemcpyAsync(e->host_st, e->st, e->count * sizeof(mg::EnsState), cudaMemcpyDeviceToHost, e->cs));
-    std::vector<cudaGraphNode_t> deps;
+    CK(cudaMemcpyAsync(e->host_stamps, e->stamps, (e->count + 1) * sizeof(unsigned long long),
+                       cudaMemcpyDeviceToHost, e->cs));
     TRY(end_segment(e, deps));
     CK(cudaGraphInstantiate(&e->exec, e->graph, 0));
     return MG_OK;
@@ -1510,6 +1571,10 @@ mg_status build_ensemble(mg_ensemble* e, const double* const* b, double* const* 
 static mg_status mg_setup_check(const mg_mesh* mesh, const mg_params* prm, const double* g, const mg_mixed* mixed);
 
 extern "C" {
+
+const char* mg_last_cuda_error(void) {
+    return g_last_cuda == cudaSuccess ? "no CUDA error" : cudaGetErrorName(g_last_cuda);
+}
 
 const char* mg_status_string(mg_status s) {
     switch (s) {
@@ -1831,18 +1896,15 @@ mg_status mg_ensemble_solve(mg_ensemble* e, mg_solve_info* infos, int32_t* statu
     if (!e) return MG_ERR_ARG;
     DeviceGuard dg(e->device);
     cudaStream_t s = S(stream);
-    CK(cudaEventRecord(e->ev_start, s));
     CK(cudaGraphLaunch(e->exec, s));
     CK(cudaStreamSynchronize(s));
     mg_status st = MG_OK;
     for (int i = 0; i < e->count; ++i) {
         const mg::EnsState& m = e->host_st[i];
         if (infos) {
-            float ms = 0.f;
-            CK(cudaEventElapsedTime(&ms, e->ev_start, e->ev_end[i]));
             infos[i].iters = m.it;
             infos[i].rel_res = m.rel;
-            infos[i].ms = ms;
+            infos[i].ms = 1e-6 * (double)(e->host_stamps[1 + i] - e->host_stamps[0]);
         }
         if (statuses) statuses[i] = m.status;
         if (st == MG_OK) st = (mg_status)m.status;
