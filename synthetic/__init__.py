@@ -147,6 +147,9 @@ CONFIGS = {
     "c192": Config("c192", n=192, nlev=70, levels=4, seed=BASE_SEED + 2),
     # C96L70 (differentiable-solve workload)
     "c96": Config("c96", n=96, nlev=70, levels=4, seed=BASE_SEED + 3),
+    # C128L70: the headline workload's shape at 44% of its size (each finest-level array still
+    # larger than L2), for detailed profiler captures
+    "c128": Config("c128", n=128, nlev=70, levels=4, seed=BASE_SEED + 5),
 }
 
 
