@@ -461,14 +461,11 @@ struct SweepRsBlocks {   // resident blocks per SM: the stash of 70 levels needs
     static constexpr int value = NLEV > 50 ? 3 : 4;
 };
 
-// SHN > 0: the neighbours' iterates and the S and W faces come instead through a register ring
-// loaded SHN steps ahead (plain and zero-start sweeps only).
-template <int NLEV, int MODE, typename B, typename O, bool BCOPY, int DEEP, int SHN = 0>
+template <int NLEV, int MODE, typename B, typename O, bool BCOPY, int DEEP>
 __global__ void __launch_bounds__(MG_SWEEP_BLOCK, SweepRsBlocks<NLEV>::value)
     k_sweep_rs(Lvl<float, float> L, const float* __restrict__ x, const float* __restrict__ xc, int ncol_c,
                const B* __restrict__ b, float* __restrict__ bcopy, O* __restrict__ xo, float omega) {
     static_assert(NLEV % 2 == 0 && NLEV >= 2, "even level count");
-    static_assert(SHN == 0 || !(MODE == XM_PROLONG || MODE == XM_PROLONG0), "register ring: no prolongation");
     constexpr int NS = NLEV / 2;
     constexpr bool PRO = (MODE == XM_PROLONG || MODE == XM_PROLONG0);
     constexpr bool RAW = (MODE == XM_PLAIN || MODE == XM_PROLONG);
@@ -525,18 +522,14 @@ __global__ void __launch_bounds__(MG_SWEEP_BLOCK, SweepRsBlocks<NLEV>::value)
         __pipeline_memcpy_async(slot(j, W_TE), L.Th + (2 * kc + fo[0]), 4);
         __pipeline_memcpy_async(slot(j, W_TN), L.Th + (2 * kc + fo[2]), 4);
         __pipeline_memcpy_async(slot(j, W_TV), L.Tv + (kc + tvo), 4);
-        if (SHN == 0) {
-            __pipeline_memcpy_async(slot(j, W_TS), L.Th + (2 * kc + fo[3]), 4);
-            if (!shWf) __pipeline_memcpy_async(slot(j, W_TW), L.Th + (2 * kc + fo[1]), 4);
-        }
+        __pipeline_memcpy_async(slot(j, W_TS), L.Th + (2 * kc + fo[3]), 4);
+        if (!shWf) __pipeline_memcpy_async(slot(j, W_TW), L.Th + (2 * kc + fo[1]), 4);
         if (RAW) {
             __pipeline_memcpy_async(slot(j, W_XN), x + (kc + dkc + c), 4);
-            if (SHN == 0) {
-                __pipeline_memcpy_async(slot(j, W_XNB), x + (kc + nb[2]), 4);
-                __pipeline_memcpy_async(slot(j, W_XS), x + (kc + nb[3]), 4);
-                if (!shE) __pipeline_memcpy_async(slot(j, W_XE), x + (kc + nb[0]), 4);
-                if (!shW) __pipeline_memcpy_async(slot(j, W_XW), x + (kc + nb[1]), 4);
-            }
+            __pipeline_memcpy_async(slot(j, W_XNB), x + (kc + nb[2]), 4);
+            __pipeline_memcpy_async(slot(j, W_XS), x + (kc + nb[3]), 4);
+            if (!shE) __pipeline_memcpy_async(slot(j, W_XE), x + (kc + nb[0]), 4);
+            if (!shW) __pipeline_memcpy_async(slot(j, W_XW), x + (kc + nb[1]), 4);
         }
         if (PRO) {
             __pipeline_memcpy_async(slot(j, W_CN), xc + (kcc + dkcc + pc), 4);
@@ -551,28 +544,6 @@ __global__ void __launch_bounds__(MG_SWEEP_BLOCK, SweepRsBlocks<NLEV>::value)
         if (i < NS) stage(i);
         __pipeline_commit();
     }
-    // register ring of the neighbour values (SHN > 0): iterates E, W, N, S and faces S, W
-    struct Nb {
-        float xh[4], ts, tw;
-    };
-    constexpr int SR = SHN > 0 ? SHN : 1;
-    Nb nr[SR];
-    auto load_nb = [&](int i, Nb& d) {
-        const unsigned kc = kc0 + (unsigned)i * dkc;
-        if (RAW) {
-            if (!shE) d.xh[0] = __ldg(x + (kc + nb[0]));
-            if (!shW) d.xh[1] = __ldg(x + (kc + nb[1]));
-            d.xh[2] = __ldg(x + (kc + nb[2]));
-            d.xh[3] = __ldg(x + (kc + nb[3]));
-        }
-        d.ts = __ldg(L.Th + (2 * kc + fo[3]));
-        if (!shWf) d.tw = __ldg(L.Th + (2 * kc + fo[1]));
-    };
-    if (SHN > 0) {
-#pragma unroll
-        for (int i = 0; i < SR; ++i)
-            if (i < NS) load_nb(i, nr[i]);
-    }
     float xprev = 0.f, x0 = 0.f, tprev = 0.f;
     if (RAW) x0 = __ldg(x + kc0 + c);
     if (PRO) x0 += __ldg(xc + kcc0 + pc);
@@ -584,28 +555,16 @@ __global__ void __launch_bounds__(MG_SWEEP_BLOCK, SweepRsBlocks<NLEV>::value)
         __pipeline_wait_prior(DEEP - 1);
         __syncwarp();   // every lane's copies of this slot are complete and visible
         const float bk = BD ? (float)rbd[(size_t)j * bd + tid] : *slot(j, W_B);
-        const float te = *slot(j, W_TE), tn = *slot(j, W_TN), tv = *slot(j, W_TV);
-        float ts, tw, xn = 0.f, xh[4] = {0.f, 0.f, 0.f, 0.f};
-        if (SHN > 0) {
-            const Nb e = nr[i % SR];
-            if (i + SR < NS) load_nb(i + SR, nr[i % SR]);
-            ts = e.ts;
-            tw = shWf ? ring[((size_t)j * NW + W_TE) * bd + tid - 1] : e.tw;
-            if (RAW) {
-#pragma unroll
-                for (int q2 = 0; q2 < 4; ++q2) xh[q2] = e.xh[q2];
-            }
-        } else {
-            ts = *slot(j, W_TS);
-            tw = shWf ? ring[((size_t)j * NW + W_TE) * bd + tid - 1] : *slot(j, W_TW);
-            if (RAW) {
-                xh[0] = *slot(j, W_XE);
-                xh[1] = *slot(j, W_XW);
-                xh[2] = *slot(j, W_XNB);
-                xh[3] = *slot(j, W_XS);
-            }
+        const float te = *slot(j, W_TE), tn = *slot(j, W_TN), tv = *slot(j, W_TV), ts = *slot(j, W_TS);
+        const float tw = shWf ? ring[((size_t)j * NW + W_TE) * bd + tid - 1] : *slot(j, W_TW);
+        float xn = 0.f, xh[4] = {0.f, 0.f, 0.f, 0.f};
+        if (RAW) {
+            xn = *slot(j, W_XN);
+            xh[0] = *slot(j, W_XE);
+            xh[1] = *slot(j, W_XW);
+            xh[2] = *slot(j, W_XNB);
+            xh[3] = *slot(j, W_XS);
         }
-        if (RAW) xn = *slot(j, W_XN);
         if (PRO) {
             xn += *slot(j, W_CN);
             xh[0] += *slot(j, W_CE);

@@ -340,10 +340,6 @@ struct SweepPF {
 #endif
 
 // The register-stash sweep (k_sweep_rs) for an FP32 level of NLEV levels, bd threads per block
-#ifndef MG_SWEEP_RS_SHN
-#define MG_SWEEP_RS_SHN 0    // > 0: the register-stash sweep loads neighbour values into a register ring
-#endif
-
 template <int NLEV, int MODE, typename B, typename O, bool BCOPY>
 mg_status launch_sweep_rs(const Lvl<float, float>& L, const float* x, const float* xc, int ncol_c, const B* b,
                           float* bcopy, O* xo, float omega, int bd, cudaStream_t s) {
@@ -353,7 +349,7 @@ mg_status launch_sweep_rs(const Lvl<float, float>& L, const float* x, const floa
     constexpr int DEEP = mg::SweepRsBlocks<NLEV>::value == 3 ? ((PRO && RAW) ? 8 : 12) : ((PRO && RAW) ? 6 : 8);
     constexpr int NW = 5 + (RAW ? 5 : 0) + (PRO ? 5 : 0) + (sizeof(B) == 8 ? 0 : 1);
     const size_t smem = (size_t)DEEP * bd * (sizeof(B) == 8 ? 8 : 0) + (size_t)DEEP * NW * bd * 4 + NLEV * 4;
-    auto kern = mg::k_sweep_rs<NLEV, MODE, B, O, BCOPY, DEEP, PRO ? 0 : MG_SWEEP_RS_SHN>;
+    auto kern = mg::k_sweep_rs<NLEV, MODE, B, O, BCOPY, DEEP>;
     if (smem > 48 * 1024) CK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     const int grid = (L.ncol + bd / 2 - 1) / (bd / 2);
     kern<<<grid, bd, smem, s>>>(L, x, xc, ncol_c, b, bcopy, xo, omega);
