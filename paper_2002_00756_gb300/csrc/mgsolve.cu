@@ -3,6 +3,7 @@
 // See include/mgsolve.h for the contract of every entry point.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <algorithm>
 #include <cmath>
@@ -225,6 +226,13 @@ mg_status upload<bf16, double>(mg_handle* h, bf16** p, const std::vector<double>
     CK(cudaMemcpy(*p, tmp.data(), tmp.size() * sizeof(bf16), cudaMemcpyHostToDevice));
     return MG_OK;
 }
+
+// An NVTX range over the scope (shows the library's calls and GCR iterations on a profiler's
+// timeline; costs nothing without a tool attached)
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+};
 
 #define TRY(call)                         \
     do {                                  \
@@ -974,6 +982,7 @@ mg_status gcr(mg_handle* h, int sys, size_t n, const double* b, double* x, doubl
     CK(cudaStreamSynchronize(s));
     gcr_started(h, g);
     while (g.active) {
+        NvtxRange it_("gcr iteration");
         TRY(gcr_launch(h, g, s, applyAS, applyP));
         CK(cudaStreamSynchronize(s));
         TRY(gcr_landed(h, g, s));
@@ -1697,6 +1706,7 @@ mg_status mg_set_pressure_solver(mg_handle* h, const mg_pressure_solver* ps) {
 }
 
 mg_status helmholtz_solve(mg_handle* h, const double* b, double* x, double* iterations, void* stream) {
+    NvtxRange nvtx_("helmholtz_solve");
     if (!h || !b || !x || b == x) return MG_ERR_ARG;
     DeviceGuard dg(h->device);
     double it = 0.0;
@@ -1744,6 +1754,7 @@ mg_status helmholtz_apply(mg_handle* h, const double* x, double* y, void* stream
 }
 
 mg_status vcycle(mg_handle* h, const double* b, double* x, void* stream) {
+    NvtxRange nvtx_("vcycle");
     if (!h || !b || !x || b == x) return MG_ERR_ARG;
     DeviceGuard dg(h->device);
     return run_vcycle(h, b, x, S(stream));
@@ -1751,6 +1762,7 @@ mg_status vcycle(mg_handle* h, const double* b, double* x, void* stream) {
 
 mg_status pressure_solve(mg_handle* h, const double* b, double* x, double tol, mg_solve_info* info,
                          void* stream) {
+    NvtxRange nvtx_("pressure_solve");
     if (!h || !b || !x || b == x || !(tol >= 0.0)) return MG_ERR_ARG;
     DeviceGuard dg(h->device);
     cudaStream_t s = S(stream);
@@ -1761,6 +1773,7 @@ mg_status pressure_solve(mg_handle* h, const double* b, double* x, double tol, m
 
 mg_status pressure_solve_adjoint(mg_handle* h, const double* g, double* lambda, double tol, mg_solve_info* info,
                                  void* stream) {
+    NvtxRange nvtx_("pressure_solve_adjoint");
     if (!h || !g || !lambda || g == lambda || !(tol >= 0.0)) return MG_ERR_ARG;
     DeviceGuard dg(h->device);
     cudaStream_t s = S(stream);
@@ -1801,6 +1814,7 @@ mg_status helmholtz_coefficient_gradient(mg_handle* h, const double* lambda, con
 mg_status ensemble_pressure_solve(mg_handle* const* handles, int32_t count, const double* const* b,
                                   double* const* x, double tol, mg_solve_info* infos, int32_t* statuses,
                                   void* stream) {
+    NvtxRange nvtx_("ensemble_pressure_solve");
     if (count < 0 || (count > 0 && (!handles || !b || !x)) || !(tol >= 0.0)) return MG_ERR_ARG;
     if (count == 0) return MG_OK;
     for (int i = 0; i < count; ++i) {
@@ -1889,6 +1903,7 @@ mg_status mg_ensemble_create(mg_handle* const* handles, int32_t count, const dou
 }
 
 mg_status mg_ensemble_solve(mg_ensemble* e, mg_solve_info* infos, int32_t* statuses, void* stream) {
+    NvtxRange nvtx_("mg_ensemble_solve");
     if (!e) return MG_ERR_ARG;
     DeviceGuard dg(e->device);
     cudaStream_t s = S(stream);
@@ -1917,6 +1932,7 @@ void mg_ensemble_destroy(mg_ensemble* e) {
 
 mg_status mixed_solve(mg_handle* h, const double* rhs_u, const double* rhs_p, double* u, double* p, double tol,
                       mg_solve_info* info, void* stream) {
+    NvtxRange nvtx_("mixed_solve");
     if (!h || !rhs_u || !rhs_p || !u || !p || !(tol >= 0.0)) return MG_ERR_ARG;
     if (!h->mixed) return MG_ERR_UNSUPPORTED;
     DeviceGuard dg(h->device);
@@ -1940,6 +1956,7 @@ mg_status mixed_solve(mg_handle* h, const double* rhs_u, const double* rhs_p, do
 
 mg_status mixed_solve_adjoint(mg_handle* h, const double* g_u, const double* g_p, double* lam_u, double* lam_p,
                               double tol, mg_solve_info* info, void* stream) {
+    NvtxRange nvtx_("mixed_solve_adjoint");
     if (!h || !g_u || !g_p || !lam_u || !lam_p || !(tol >= 0.0)) return MG_ERR_ARG;
     if (!h->mixed) return MG_ERR_UNSUPPORTED;
     DeviceGuard dg(h->device);
@@ -2054,6 +2071,7 @@ mg_status schur_precond(mg_handle* h, const double* ru, const double* rp, double
 }
 
 mg_status mg_autotune(mg_handle* h, int32_t* choices, void* stream) {
+    NvtxRange nvtx_("mg_autotune");
     if (!h) return MG_ERR_ARG;
     if (h->prof || h->nine) return MG_ERR_UNSUPPORTED;   // the tuner uses the per-launch profiler itself
     DeviceGuard dg(h->device);
