@@ -589,7 +589,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="c192")
-    ap.add_argument("--precision", default="fp32", choices=["fp64", "fp32", "fp32_bf16"])
+    ap.add_argument("--precision", default="fp32", choices=["fp64", "fp32", "fp32_p64", "fp32_bf16"])
     ap.add_argument("--dt", type=float, default=None,
                     help="time step in s (default: the workload's, 600 s; 1200 s gives CFL_h ~ 7.9 at C192, "
                          "the paper's regime for the robustness sweep)")
@@ -604,6 +604,8 @@ def main():
     ap.add_argument("--rotation", type=float, default=0.0,
                     help="mixed system: planet angular velocity [1/s] of the implicit Coriolis term")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-compare-precisions", dest="compare_precisions", action="store_false",
+                    help="skip timing the FP64-pivot and plain FP64 V-cycle solves beside the FP32 one")
     ap.add_argument("--profile-solve", action="store_true",
                     help="untimed: one pressure solve limited to --iters GCR iterations (for ncu captures)")
     ap.add_argument("--iters", type=int, default=2)
@@ -729,6 +731,27 @@ def main():
         torch.cuda.synchronize()
     e2e_ms = job_ms_per_unit(max_over_ranks((time.perf_counter() - t0) * 1e3, pg, "cuda"), e2e_steps, world)
 
+    # ---- the same solve with the finest level eliminated in FP64 (MG_FP32_P64) and with the
+    # plain FP64 V-cycle, a few solves each, timed the same way ----
+    compare = {}
+    if args.precision == "fp32" and args.compare_precisions:
+        for prec in ("fp32_p64", "fp64"):
+            hc = mg.mg_setup_config(cfg, inp, precision=prec)
+            xc = torch.zeros_like(b)
+            for _ in range(2):
+                mg.pressure_solve(hc, b, xc, tol=args.tol)
+            torch.cuda.synchronize()
+            c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            nc = 3
+            c0.record(stream)
+            for _ in range(nc):
+                ic = mg.pressure_solve(hc, b, xc, tol=args.tol)
+            c1.record(stream)
+            torch.cuda.synchronize()
+            compare[prec] = {"ms_per_solve": round(c0.elapsed_time(c1) / nc, 3), "iters": ic.iters,
+                             "rel_res": float(f"{ic.rel_res:.3e}")}
+            hc.destroy()
+
     # ---- roofline of the dominant kernel: K more solves, timed the same way, with CUDA
     # events around every launch of the dominant kernel's kind and level (the solves then
     # run as plain launches instead of the cached per-iteration graphs) ----
@@ -788,6 +811,9 @@ def main():
                      "vcycle_GBps": round(vc_bytes / (vc_ms * 1e-3) / 1e9, 1),
                      "vcycle_frac": round(vc_bytes / (vc_ms * 1e-3) / 1e9 / peak, 4)},
         "gpu_launches": len(all_recs) // n_prof * args.steps,
+        **({"compare_precisions": {"note": "the same solve, 3 timed after 2 untimed; fp32_p64: FP32 V-cycle "
+                                           "with the finest level's column elimination in FP64; fp64: the "
+                                           "plain FP64 V-cycle", **compare}} if compare else {}),
         "kernels": {"note": f"per solve, from {n_prof} untimed solves with every launch event-timed", **breakdown},
         "clocks": clk.result,
     }

@@ -70,7 +70,11 @@ typedef enum {
 enum {
     MG_FP64 = 0,            /* FP64 vectors and coefficients (the plain method) */
     MG_FP32 = 1,            /* FP32 vectors, coefficients and accumulation */
-    MG_FP32_BF16COEF = 2    /* FP32 vectors and accumulation, BF16 stored coefficients */
+    MG_FP32_BF16COEF = 2,   /* FP32 vectors and accumulation, BF16 stored coefficients */
+    MG_FP32_P64 = 3         /* MG_FP32, but the finest level's column elimination (Thomas pivots,
+                               eliminated right-hand side, multipliers) runs in FP64 on the FP32
+                               data; the stash and back substitution stay FP32.  Not with
+                               mg_setup_9pt (MG_ERR_UNSUPPORTED) */
 };
 
 typedef struct {
@@ -86,7 +90,7 @@ typedef struct {
     double omega;                /* over-relaxation of the block-Jacobi sweep (Eq. jacobi) */
     int32_t n_pre, n_post;       /* smoothing sweeps before / after the coarse correction */
     int32_t n_coarse;            /* sweeps from zero on the coarsest level */
-    int32_t vcycle_precision;    /* MG_FP64 | MG_FP32 | MG_FP32_BF16COEF */
+    int32_t vcycle_precision;    /* MG_FP64 | MG_FP32 | MG_FP32_BF16COEF | MG_FP32_P64 */
     int32_t gcr_restart;         /* GCR directions kept before a restart, 1..MG_MAX_RESTART */
     int32_t max_iter;            /* Krylov iteration limit */
 } mg_params;

@@ -20,8 +20,8 @@ from .build import LIB as _LIB_PATH
 
 MG_OK, MG_ERR_ARG, MG_ERR_CUDA, MG_ERR_NOMEM = 0, -1, -2, -3
 MG_ERR_NOT_CONVERGED, MG_ERR_BREAKDOWN, MG_ERR_TIMEOUT, MG_ERR_UNSUPPORTED = -4, -5, -6, -7
-MG_FP64, MG_FP32, MG_FP32_BF16COEF = 0, 1, 2
-PRECISIONS = {"fp64": MG_FP64, "fp32": MG_FP32, "fp32_bf16": MG_FP32_BF16COEF}
+MG_FP64, MG_FP32, MG_FP32_BF16COEF, MG_FP32_P64 = 0, 1, 2, 3
+PRECISIONS = {"fp64": MG_FP64, "fp32": MG_FP32, "fp32_bf16": MG_FP32_BF16COEF, "fp32_p64": MG_FP32_P64}
 
 
 class MGError(RuntimeError):

@@ -166,12 +166,17 @@ struct SweepShal {
 #ifndef MG_SWEEP_WARP_HALVES
 #define MG_SWEEP_WARP_HALVES 1
 #endif
-template <typename T, typename C, int MODE, typename X, typename B, typename O, bool BCOPY, int DEEP, int SHAL>
+// P is the type of the column elimination (pivots, eliminated right-hand side, multipliers and
+// the interface solve); P = T everywhere but in the finest-level sweeps of MG_FP32_P64, which
+// eliminate FP32 data with FP64 pivots.  The stash (w_i, e_i) and the back substitution stay in T.
+template <typename T, typename C, int MODE, typename X, typename B, typename O, bool BCOPY, int DEEP, int SHAL,
+          typename P>
 __global__ void __launch_bounds__(MG_SWEEP_BLOCK, 4) k_sweep(Lvl<T, C> L, const X* __restrict__ x, const T* __restrict__ xc,
                         int ncol_c, const B* __restrict__ b, T* __restrict__ bcopy,
                         O* __restrict__ xo, T omega) {
     static_assert(DEEP % SHAL == 0, "ring lengths");
     static_assert(sizeof(X) == sizeof(T), "iterate type");
+    static_assert(DEEP * (sizeof(B) + sizeof(T)) >= 3 * sizeof(P), "the interface exchange reuses the ring");
     // asynchronous copies move 4, 8 or 16 bytes: a BF16 coefficient travels in the aligned
     // 4-byte pair that holds it (its neighbour in memory rides along) and is picked out of
     // the pair in the ring
@@ -310,7 +315,7 @@ __global__ void __launch_bounds__(MG_SWEEP_BLOCK, 4) k_sweep(Lvl<T, C> L, const 
     T xprev = T(0), x0 = T(0), tprev = T(0);
     if (RAW) x0 = ldx<T>(px + kc0);
     if (PRO) x0 += __ldg(pcc + kcc0);
-    T q = T(0), ip = T(0), y = T(0), anext = T(0);
+    P q = P(0), ip = P(0), y = P(0), anext = P(0);
     T* psc = sc + tid;
     T* pse = se + tid;
     const T* prdz = srdz + kfirst;
@@ -372,15 +377,15 @@ __global__ void __launch_bounds__(MG_SWEEP_BLOCK, 4) k_sweep(Lvl<T, C> L, const 
                 hx += e.ts * (x0 - xh[3]);
                 r -= x0 + (rA * hx + rdz * (tv * (x0 - xn) + tprev * (x0 - xprev)));
             }
-            anext = rdz * tv;
-            const T m = (rdz * tprev) * ip;
-            q = (T(1) + rA * ((te + tw) + (tn + e.ts))) + m * q;
-            const T p = q + anext;
-            y = r + m * y;
-            ip = T(1) / p;
-            const T ei = anext * ip;
-            *psc = x0 + omega * (y * ip) - ei * xn;
-            *pse = ei;
+            anext = P(rdz) * P(tv);
+            const P m = (P(rdz) * P(tprev)) * ip;
+            q = (P(1) + P(rA) * P((te + tw) + (tn + e.ts))) + m * q;
+            const P p = q + anext;
+            y = P(r) + m * y;
+            ip = P(1) / p;
+            const P ei = anext * ip;
+            *psc = T(P(x0) + P(omega) * (y * ip) - ei * P(xn));
+            *pse = T(ei);
             xprev = x0;
             x0 = xn;
             tprev = tv;
@@ -408,28 +413,28 @@ __global__ void __launch_bounds__(MG_SWEEP_BLOCK, 4) k_sweep(Lvl<T, C> L, const 
     // through shared memory (the ring, free once every warp has left it) from the thread
     // tid ^ (bd / 2) that holds the other half of the column
     __syncthreads();
-    T* xch = reinterpret_cast<T*>(smem_raw);
+    P* xch = reinterpret_cast<P*>(smem_raw);
     xch[tid] = q;
     xch[bd + tid] = y;
     xch[2 * bd + tid] = anext;
     __syncthreads();
     const int pt = tid ^ (bd >> 1);
-    const T qo = xch[pt], yo = xch[bd + pt], ao = xch[2 * bd + pt];
+    const P qo = xch[pt], yo = xch[bd + pt], ao = xch[2 * bd + pt];
 #else
-    const T qo = __shfl_xor_sync(0xffffffffu, q, 16);
-    const T yo = __shfl_xor_sync(0xffffffffu, y, 16);
-    const T ao = __shfl_xor_sync(0xffffffffu, anext, 16);
+    const P qo = __shfl_xor_sync(0xffffffffu, q, 16);
+    const P yo = __shfl_xor_sync(0xffffffffu, y, 16);
+    const P ao = __shfl_xor_sync(0xffffffffu, anext, 16);
 #endif
-    T dlt;
+    P dlt;
     if (nlev - hsteps == 0) {
         dlt = y * ip;   // a single level: nothing above, anext = 0
     } else {
-        const T po = qo + ao;
+        const P po = qo + ao;
         dlt = (y * po + anext * yo) / (q * po + anext * qo);
     }
     if (!active || nsteps == 0) return;
     // xprev holds the iterate at the last level of this half: out = x + omega d there
-    T out = xprev + omega * dlt;
+    T out = T(P(xprev) + P(omega) * dlt);
     O* po = xo + c;
     unsigned ko = kc0 + (unsigned)(nsteps - 1) * dkc;
     po[ko] = (O)out;

@@ -113,6 +113,7 @@ struct mg_handle {
     float* rdz32 = nullptr;
     double* a6 = nullptr;       // finest level: six premultiplied FP64 couplings and 1 + their sum, per cell
     bool nine = false;          // 9-cell stencil (mg_setup_9pt)
+    bool pivot64 = false;       // MG_FP32_P64: FP64 elimination in the finest level's FP32 sweeps
     double* area0 = nullptr;    // finest level: column areas and layer depths (cell volumes, adjoint solve)
     double* dz = nullptr;
     double* adj = nullptr;      // [N] the scaled right-hand side of the adjoint solve
@@ -365,6 +366,10 @@ mg_status launch_sweep_rs(const Lvl<float, float>& L, const float* x, const floa
     return MG_OK;
 }
 
+template <typename T, typename C, int MODE, typename X, typename B, typename O, bool BCOPY, typename P>
+mg_status launch_sweep_shared(mg_handle* h, int lev, const Lvl<T, C>& L, const X* x, const T* xc, int ncol_c,
+                              const B* b, T* bcopy, O* xo, double omega, cudaStream_t s);
+
 template <typename T, typename C, int MODE, typename X, typename B, typename O, bool BCOPY>
 mg_status launch_sweep(mg_handle* h, int lev, const Lvl<T, C>& L, const X* x, const T* xc, int ncol_c,
                        const B* b, T* bcopy, O* xo, double omega, cudaStream_t s) {
@@ -374,6 +379,12 @@ mg_status launch_sweep(mg_handle* h, int lev, const Lvl<T, C>& L, const X* x, co
     if (MODE == mg::XM_PROLONG || MODE == mg::XM_PROLONG0) per += 0.25 * sizeof(T);
     if (BCOPY) per += sizeof(T);
     Prof pr(h, MG_K_SWEEP, lev, nc * per, s, MODE);
+    if constexpr (std::is_same<T, float>::value && std::is_same<C, float>::value) {
+        // MG_FP32_P64: the finest level eliminates with FP64 pivots
+        if (h && h->pivot64 && lev == 0)
+            return launch_sweep_shared<T, C, MODE, X, B, O, BCOPY, double>(h, lev, L, x, xc, ncol_c, b, bcopy, xo,
+                                                                          omega, s);
+    }
     if constexpr (MG_SWEEP_REG && std::is_same<T, float>::value && std::is_same<C, float>::value &&
                   std::is_same<X, float>::value && (MODE == mg::XM_ZERO || MODE == mg::XM_PLAIN)) {
         const int bdr = (h && h->lv[lev].sweep_bd > 0) ? h->lv[lev].sweep_bd : MG_SWEEP_BLOCK;
@@ -385,6 +396,13 @@ mg_status launch_sweep(mg_handle* h, int lev, const Lvl<T, C>& L, const X* x, co
             default: break;
         }
     }
+    return launch_sweep_shared<T, C, MODE, X, B, O, BCOPY, T>(h, lev, L, x, xc, ncol_c, b, bcopy, xo, omega, s);
+}
+
+// the shared-memory-stash sweep (k_sweep), elimination in P
+template <typename T, typename C, int MODE, typename X, typename B, typename O, bool BCOPY, typename P>
+mg_status launch_sweep_shared(mg_handle* h, int lev, const Lvl<T, C>& L, const X* x, const T* xc, int ncol_c,
+                              const B* b, T* bcopy, O* xo, double omega, cudaStream_t s) {
     // two threads per column; per thread the shared memory holds the asynchronous-copy
     // ring (DEEP slots of b, the next iterate and, unless BF16, three coefficients) and the
     // stash (2 values per step of half a column); it must fit the budget
@@ -413,7 +431,7 @@ mg_status launch_sweep(mg_handle* h, int lev, const Lvl<T, C>& L, const X* x, co
     constexpr int SHAL = MODE == mg::XM_PROLONG ? MG_SWEEP_SHAL_PRO
                          : MODE == mg::XM_ZERO    ? (sizeof(T) == 8 ? 2 : MG_SWEEP_SHAL_ZERO)
                                                   : SweepPF<T>::shal;
-    auto kern = mg::k_sweep<T, C, MODE, X, B, O, BCOPY, DEEP, SHAL>;
+    auto kern = mg::k_sweep<T, C, MODE, X, B, O, BCOPY, DEEP, SHAL, P>;
     if (smem > 48 * 1024) CK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     const int cols = bd / 2;
     const int grid = (L.ncol + cols - 1) / cols;
@@ -664,13 +682,14 @@ mg_status run_cycle(mg_handle* h, const Cycle& cy, const double* b, double* x, c
     if (h->nine) {
         switch (h->prm.vcycle_precision) {
             case MG_FP64: return mgv9<double, double, double>(h, cy, 0, b, x, s);
-            case MG_FP32: return mgv9<float, double, double>(h, cy, 0, b, x, s);
+            case MG_FP32: return mgv9<float, double, double>(h, cy, 0, b, x, s);   // (MG_FP32_P64: not built)
             default: return MG_ERR_UNSUPPORTED;
         }
     }
     switch (h->prm.vcycle_precision) {
         case MG_FP64: return mgv<double, double, double, double>(h, cy, 0, b, x, s);
-        case MG_FP32: return mgv<float, float, double, double>(h, cy, 0, b, x, s);
+        case MG_FP32:
+        case MG_FP32_P64: return mgv<float, float, double, double>(h, cy, 0, b, x, s);
         case MG_FP32_BF16COEF: return mgv<float, bf16, double, double>(h, cy, 0, b, x, s);
         default: return MG_ERR_ARG;
     }
@@ -1214,7 +1233,9 @@ mg_status setup_impl(mg_handle* h, const mg_mesh* mesh, const mg_params* prm, co
     TRY(upload(h, &h->faceSide0, hg[0].faceSide));
     TRY(upload(h, &h->nbrSide0, hg[0].nbr_side));
     TRY(dalloc(h, &h->flag, 1));
-    const int prec = prm->vcycle_precision;
+    // MG_FP32_P64 stores and computes as MG_FP32; only the finest level's elimination differs
+    const int prec = prm->vcycle_precision == MG_FP32_P64 ? MG_FP32 : prm->vcycle_precision;
+    h->pivot64 = prm->vcycle_precision == MG_FP32_P64;
     h->lv.resize(L);
     for (int l = 0; l < L; ++l) {
         DevLevel& d = h->lv[l];
@@ -1620,7 +1641,7 @@ static mg_status mg_setup_check(const mg_mesh* mesh, const mg_params* prm, const
     if (prm->levels < 1 || prm->levels > MG_MAX_LEVELS) return MG_ERR_ARG;
     if (mesh->n % (1 << (prm->levels - 1)) != 0) return MG_ERR_ARG;
     if (!std::isfinite(prm->omega) || prm->n_pre < 0 || prm->n_post < 0 || prm->n_coarse < 1) return MG_ERR_ARG;
-    if (prm->vcycle_precision < MG_FP64 || prm->vcycle_precision > MG_FP32_BF16COEF) return MG_ERR_ARG;
+    if (prm->vcycle_precision < MG_FP64 || prm->vcycle_precision > MG_FP32_P64) return MG_ERR_ARG;
     if (prm->gcr_restart < 1 || prm->gcr_restart > MG_MAX_RESTART || prm->max_iter < 1) return MG_ERR_ARG;
     if (mixed && (!mixed->beta_up || !mixed->beta_dn || !std::isfinite(mixed->eps) || mixed->eps < 0.0 ||
                   (mixed->consistent != 0 && mixed->consistent != 1) || !std::isfinite(mixed->coriolis_f0) ||
@@ -1637,7 +1658,8 @@ mg_status mg_setup_9pt(const mg_mesh* mesh, const mg_params* prm, const double* 
     if (!out) return MG_ERR_ARG;
     *out = nullptr;
     if (!(gamma2 > 0.0) || !std::isfinite(gamma2) || !prm) return MG_ERR_ARG;
-    if (prm->vcycle_precision == MG_FP32_BF16COEF) return MG_ERR_UNSUPPORTED;
+    if (prm->vcycle_precision == MG_FP32_BF16COEF || prm->vcycle_precision == MG_FP32_P64)
+        return MG_ERR_UNSUPPORTED;
     if (!mesh || !g || !mesh->z_interfaces) return MG_ERR_ARG;
     mg_handle* h = nullptr;
     // validate exactly as mg_setup does, then build with the next-to-nearest fluxes

@@ -8,8 +8,10 @@ reach the launch shapes only large levels use.
   shapes), so a wrong neighbour, face or child anywhere (e.g. along one panel edge) fails.
 * FP32 V-cycles at C96L20 (55,296 columns: the copy-ring residual + restriction) and C144L12
   (124,416 columns: 24 levels per thread, one ragged chunk), per element.
-* The FP32 V-cycle (FP32 Thomas pivots on every level) against the FP64 one (FP64 pivots), per
-  element, and both preconditioned solves' iteration counts and errors against the oracle.
+* The FP32 V-cycle (FP32 Thomas pivots on every level) against the FP64 one (FP64 pivots) and
+  against MG_FP32_P64 (FP32 data, FP64 elimination on the finest level), per element, and the
+  preconditioned solves' iteration counts and errors against the oracle; the same V-cycle
+  comparison at the largest time step of the CFL study (dt = 1200 s, CFL_h about 7.9).
 * The exact solve bench.py times (FP32 V-cycle, tol SOLVE_TOL, x0 = 0): true residual and
   relative error against the oracle's solution x* (oracle GCR on its own operator to a
   relative residual of 1e-11) <= 1e-8.
@@ -82,7 +84,7 @@ def test_vcycle_full_size(setup):
     mg, cfg, inp, hier = setup
     ref = hier.vcycle(inp["rhs"], cfg.omega, cfg.n_pre, cfg.n_post, cfg.n_coarse).ravel()
     out = {}
-    for prec, tol in (("fp64", 1e-11), ("fp32", FP32_VCYCLE_ELEMENT)):
+    for prec, tol in (("fp64", 1e-11), ("fp32", FP32_VCYCLE_ELEMENT), ("fp32_p64", FP32_VCYCLE_ELEMENT)):
         h = mg.mg_setup_config(cfg, inp, precision=prec)
         x = torch.empty(cfg.ncell, dtype=torch.float64, device="cuda")
         mg.vcycle(h, dev(inp["rhs"]), x)
@@ -92,10 +94,33 @@ def test_vcycle_full_size(setup):
         print(f"C192L70 {prec} V-cycle vs oracle: relative 2-norm {err:.3e}, worst element {el:.3e} of max")
         assert el <= tol
         h.destroy()
-    # FP32 pivots (FP32 V-cycle) against FP64 pivots (FP64 V-cycle), element by element
-    el = element_err(out["fp32"], out["fp64"])
-    print(f"C192L70 FP32 V-cycle vs FP64 V-cycle: worst element {el:.3e} of max")
-    assert el <= FP32_VCYCLE_ELEMENT
+    # FP32 pivots (FP32 V-cycle) against FP64 pivots (FP64 V-cycle; FP32 V-cycle with the finest
+    # level eliminated in FP64), element by element
+    for a, b in (("fp32", "fp64"), ("fp32_p64", "fp64"), ("fp32", "fp32_p64")):
+        el = element_err(out[a], out[b])
+        print(f"C192L70 {a} V-cycle vs {b} V-cycle: worst element {el:.3e} of max")
+        assert el <= FP32_VCYCLE_ELEMENT
+    assert not np.array_equal(out["fp32"], out["fp32_p64"])   # the FP64 elimination ran
+
+
+def test_pivot_precision_at_largest_time_step(setup):
+    """dt = 1200 s (CFL_h about 7.9, the paper's C192 time step): the V-cycle with FP32 pivots,
+    with the finest level's elimination in FP64, and in FP64 throughout, element by element."""
+    import dataclasses
+    mg, cfg, inp, _ = setup
+    cfg = dataclasses.replace(cfg, dt=1200.0)
+    inp = syn.make_inputs(cfg)
+    out = {}
+    for prec in ("fp64", "fp32", "fp32_p64"):
+        h = mg.mg_setup_config(cfg, inp, precision=prec)
+        x = torch.empty(cfg.ncell, dtype=torch.float64, device="cuda")
+        mg.vcycle(h, dev(inp["rhs"]), x)
+        out[prec] = host(x)
+        h.destroy()
+    for a in ("fp32", "fp32_p64"):
+        el = element_err(out[a], out["fp64"])
+        print(f"C192L70 dt 1200 s: {a} V-cycle vs fp64 V-cycle: worst element {el:.3e} of max")
+        assert el <= FP32_VCYCLE_ELEMENT
 
 
 @pytest.mark.parametrize("n,nlev", [(96, 20), (144, 12)])
@@ -134,7 +159,7 @@ def test_benchmarked_solve_error(setup):
     from bench import SOLVE_TOL
     mg, cfg, inp, hier = setup
     xs = oracle_solution(cfg, inp, hier)
-    for prec in ("fp32", "fp64"):
+    for prec in ("fp32", "fp32_p64", "fp64"):
         h = mg.mg_setup_config(cfg, inp, precision=prec)
         x = torch.zeros(cfg.ncell, dtype=torch.float64, device="cuda")
         info = mg.pressure_solve(h, dev(inp["rhs"]), x, tol=SOLVE_TOL)

@@ -187,8 +187,10 @@ def test_unsupported_calls(mg):
         mg.mg_autotune(h)
     with pytest.raises(mg.MGError):
         mg.mg_smooth_noalloc(h, 0, v, None, v.clone(), 1)
-    with pytest.raises(mg.MGError):
-        mg.mg_setup_config(cfg, inp, precision="fp32_bf16")
+    for prec in ("fp32_bf16", "fp32_p64"):
+        with pytest.raises(mg.MGError) as e:
+            mg.mg_setup_config(cfg, inp, precision=prec)
+        assert e.value.status == mg.MG_ERR_UNSUPPORTED
     import ctypes
     out = ctypes.c_void_p()
     prm = mg._Params(2, 0.8, 2, 2, 4, 0, 5, 10)

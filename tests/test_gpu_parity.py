@@ -168,7 +168,7 @@ def test_vcycle_smoothing_counts(mg, n_pre, n_post, n_coarse):
     assert np.linalg.norm(host(x) - ref) <= 1e-12 * np.linalg.norm(ref)
 
 
-@pytest.mark.parametrize("precision,tol", [("fp32", 1e-4), ("fp32_bf16", 5e-2)])
+@pytest.mark.parametrize("precision,tol", [("fp32", 1e-4), ("fp32_p64", 1e-4), ("fp32_bf16", 5e-2)])
 @pytest.mark.parametrize("name", ["c12", "c20l9", "c5l3", "c2l3"])
 def test_vcycle_reduced_precision(mg, name, precision, tol):
     cfg, inp, hier = problem(name)
@@ -190,19 +190,20 @@ def test_vcycle_reduced_precision(mg, name, precision, tol):
 CASES["c66l9"] = (syn.small_config(66, 9, levels=2, seed=syn.BASE_SEED + 15), None)
 
 
+@pytest.mark.parametrize("precision", ["fp32", "fp32_p64"])
 @pytest.mark.parametrize("n_pre,n_post,n_coarse", [(2, 2, 4), (0, 2, 4), (1, 3, 1), (2, 0, 2)])
-def test_vcycle_fp32_large_ragged_level(mg, n_pre, n_post, n_coarse):
+def test_vcycle_fp32_large_ragged_level(mg, n_pre, n_post, n_coarse, precision):
     cfg, inp, hier = problem("c66l9")
     assert cfg.ncol >= 128 * 150 and cfg.ncol % 64 != 0 and cfg.nlev % 2 == 1
     h = mg.mg_setup(cfg.n, cfg.nlev, inp["z_if"], inp["g"], radius=cfg.radius, cs_dt=cfg.cs * cfg.dt,
                     levels=cfg.levels, omega=cfg.omega, n_pre=n_pre, n_post=n_post, n_coarse=n_coarse,
-                    precision="fp32")
+                    precision=precision)
     b = inp["rhs"]
     x = torch.empty(cfg.ncell, dtype=torch.float64, device="cuda")
     mg.vcycle(h, dev(b), x)
     ref = hier.vcycle(b, cfg.omega, n_pre, n_post, n_coarse).ravel()
     err = np.linalg.norm(host(x) - ref) / np.linalg.norm(ref)
-    print(f"c66l9 fp32 V-cycle ({n_pre},{n_post},{n_coarse}) relative error vs FP64 oracle: {err:.3e}")
+    print(f"c66l9 {precision} V-cycle ({n_pre},{n_post},{n_coarse}) relative error vs FP64 oracle: {err:.3e}")
     assert err <= 2e-6
 
 
@@ -215,7 +216,7 @@ def _xstar(name):
     return _cache[key]
 
 
-@pytest.mark.parametrize("precision", ["fp64", "fp32", "fp32_bf16"])
+@pytest.mark.parametrize("precision", ["fp64", "fp32", "fp32_p64", "fp32_bf16"])
 @pytest.mark.parametrize("name", ["c12", "c20l9", "c5l3", "c2l3", "c1l4"])
 def test_pressure_solve(mg, name, precision):
     from oracle.krylov import gcr

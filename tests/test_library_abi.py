@@ -41,6 +41,15 @@ def test_status_strings(lib):
     assert mg.status_string(5) == "unknown status"
 
 
+def test_precision_constants_match_the_header():
+    import paper_2002_00756_gb300 as mg
+    hdr = open(HEADER).read()
+    for name in ("MG_FP64", "MG_FP32", "MG_FP32_BF16COEF", "MG_FP32_P64"):
+        m = re.search(name + r"\s*=\s*(\d+)", hdr)
+        assert m and int(m.group(1)) == getattr(mg, name), name
+    assert set(mg.PRECISIONS.values()) == {0, 1, 2, 3}
+
+
 def _setup_raw(lib, n=4, nlev=3, levels=2, precision=0, restart=5, max_iter=10, n_coarse=4, g=None,
                null_mesh=False, mixed=None):
     import paper_2002_00756_gb300 as mg
@@ -64,6 +73,8 @@ def _setup_raw(lib, n=4, nlev=3, levels=2, precision=0, restart=5, max_iter=10, 
     dict(n=6, levels=3),          # 6 is not divisible by 2^(3-1)
     dict(levels=0),
     dict(precision=7),
+    dict(precision=4),            # one past MG_FP32_P64
+    dict(precision=-1),
     dict(restart=0),
     dict(restart=17),
     dict(max_iter=0),
