@@ -148,6 +148,29 @@ def test_coarse_face_factor_is_the_edge_weighted_mean_of_its_fine_faces():
         assert np.allclose(h.levels[1].mu_h[d], h.levels[1].mu_h[coarse.nbr_dir[d], coarse.nbr[d]], rtol=1e-14)
 
 
+def test_coarse_face_field_conserves_edge_integrals():
+    """restrict_side_field against geometry alone.  For every coarse cell and side, the children
+    whose neighbour on that side lies outside the cell (found from the fine mesh's connectivity,
+    not from the child numbering) are the two fine faces that make up the coarse face: their
+    great-circle lengths add up to the coarse mesh's own edge length, and the restricted value
+    conserves the edge integral, L_C f_C = sum_f l_f f_f.  A constant restricts to itself."""
+    from oracle.multigrid import restrict_side_field
+    z = np.linspace(0.0, 1000.0, 3)
+    fine, coarse = Mesh(8, z, R), Mesh(4, z, R)
+    parent = fine.parent()
+    f = syn.normal(77, 0, 4 * fine.ncol).reshape(4, fine.ncol)
+    out = restrict_side_field(fine, coarse, f)
+    for d in range(4):
+        for C in range(coarse.ncol):
+            kids = np.nonzero(parent == C)[0]
+            side = [k for k in kids if parent[fine.nbr[d][k]] != C]
+            assert len(side) == 2
+            lf = fine.edge_len[d][side]
+            assert lf.sum() == pytest.approx(coarse.edge_len[d][C], rel=1e-12)
+            assert coarse.edge_len[d][C] * out[d][C] == pytest.approx(float(np.dot(lf, f[d][side])), rel=1e-12)
+    assert np.allclose(restrict_side_field(fine, coarse, np.full((4, fine.ncol), 2.5)), 2.5, rtol=1e-15)
+
+
 def test_mixed_gcr_with_consistent_mass_and_rotation_matches_direct_solve():
     """GCR(5) with the lumped Schur-complement MG preconditioner on the full M2^{mu,C}
     system (Earth's rotation, tau_u dt 2 Omega = 0.0437) converges to the direct solution."""
