@@ -335,7 +335,7 @@ def test_mixed_apply_and_schur(mg, name):
     assert np.linalg.norm(got - pref) <= 1e-11 * np.linalg.norm(pref)
 
 
-@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+@pytest.mark.parametrize("precision", ["fp64", "fp32", "fp32_p64"])
 @pytest.mark.parametrize("name", list(MIXED))
 def test_mixed_solve(mg, name, precision):
     from oracle.reference import assemble_mixed, direct_solve, iterative_reference
@@ -361,7 +361,7 @@ def test_mixed_solve(mg, name, precision):
     assert err <= 1e-8 and perr <= 1e-8
 
 
-@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+@pytest.mark.parametrize("precision", ["fp64", "fp32", "fp32_p64"])
 def test_solve_is_scale_invariant(mg, precision):
     """H x = 2^-70 b gives 2^-70 x, bit for bit, in the same iterations: every scalar of GCR and
     every value of the V-cycle scales by a power of two (residual norms down to 1e-30 and
