@@ -169,7 +169,7 @@ def test_vcycle_smoothing_counts(mg, n_pre, n_post, n_coarse):
 
 
 @pytest.mark.parametrize("precision,tol", [("fp32", 1e-4), ("fp32_p64", 1e-4), ("fp32_bf16", 5e-2)])
-@pytest.mark.parametrize("name", ["c12", "c20l9", "c5l3", "c2l3"])
+@pytest.mark.parametrize("name", ["c12", "c20l9", "c5l3", "c2l3", "c4l1", "c2l1"])
 def test_vcycle_reduced_precision(mg, name, precision, tol):
     cfg, inp, hier = problem(name)
     h = mg.mg_setup_config(cfg, inp, precision=precision)
