@@ -199,6 +199,17 @@ const char* mg_status_string(mg_status s);
  * is reported, so it does not surface again in a later call. */
 const char* mg_last_cuda_error(void);
 
+/* Test hooks for the error paths (failure detection by host-side injection; no GPU fault).
+ * mg_inject_alloc_failure(n), n > 0: the n-th device or pinned-host allocation the library
+ * attempts after this call fails as if memory were exhausted, and the call making it returns
+ * MG_ERR_NOMEM after releasing everything it had allocated; n <= 0 turns injection off.
+ * Returns the number of allocations attempted since the previous call (so a set-up run between
+ * two calls counts its allocations).  Process-wide; not for concurrent set-ups.
+ * mg_live_allocations: the library's live device and pinned-host allocations over all handles
+ * and ensembles (a leak check: it returns to its earlier value once they are destroyed). */
+int64_t mg_inject_alloc_failure(int64_t nth);
+int64_t mg_live_allocations(void);
+
 /* Sizes of the handle's problem: ncol and N of the finest level, velocity unknowns
  * (0 without mixed data).  Any pointer may be NULL. */
 mg_status mg_sizes(const mg_handle* h, int64_t* ncol, int64_t* ncell, int64_t* nu);

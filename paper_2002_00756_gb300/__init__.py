@@ -132,6 +132,10 @@ def load() -> ctypes.CDLL:
         lib.mg_status_string.restype = ctypes.c_char_p
         lib.mg_last_cuda_error.argtypes = []
         lib.mg_last_cuda_error.restype = ctypes.c_char_p
+        lib.mg_inject_alloc_failure.argtypes = [ctypes.c_int64]
+        lib.mg_inject_alloc_failure.restype = ctypes.c_int64
+        lib.mg_live_allocations.argtypes = []
+        lib.mg_live_allocations.restype = ctypes.c_int64
         _lib = lib
     return _lib
 

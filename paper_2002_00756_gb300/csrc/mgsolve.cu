@@ -6,6 +6,7 @@
 #include <nvtx3/nvToolsExt.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -193,15 +194,42 @@ thread_local cudaError_t g_last_cuda = cudaSuccess;
         }                              \
     } while (0)
 
+// Every device and pinned-host allocation of the library goes through mem_alloc / mem_free.
+// They count the live allocations (mg_live_allocations) and carry the failure injection of
+// mg_inject_alloc_failure: with g_fail_at = n > 0, the n-th allocation attempted after the call
+// fails as if the memory were exhausted.
+std::atomic<long long> g_fail_at{0}, g_alloc_seen{0}, g_live{0};
+
+enum MemKind { MEM_DEVICE, MEM_PINNED };
+
+bool mem_alloc(void** p, size_t bytes, MemKind kind) {
+    *p = nullptr;
+    const long long seen = g_alloc_seen.fetch_add(1) + 1;
+    const long long at = g_fail_at.load();
+    if (at > 0 && seen == at) return false;
+    const cudaError_t e = kind == MEM_DEVICE ? cudaMalloc(p, bytes) : cudaMallocHost(p, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        *p = nullptr;
+        return false;
+    }
+    g_live.fetch_add(1);
+    return true;
+}
+
+void mem_free(void* p, MemKind kind) {
+    if (!p) return;
+    if (kind == MEM_DEVICE) cudaFree(p);
+    else cudaFreeHost(p);
+    g_live.fetch_sub(1);
+}
+
 template <typename P>
 mg_status dalloc(mg_handle* h, P** p, size_t count) {
     *p = nullptr;
     if (count == 0) return MG_OK;
     void* q = nullptr;
-    if (cudaMalloc(&q, count * sizeof(P)) != cudaSuccess) {
-        cudaGetLastError();
-        return MG_ERR_NOMEM;
-    }
+    if (!mem_alloc(&q, count * sizeof(P), MEM_DEVICE)) return MG_ERR_NOMEM;
     h->allocs.push_back(q);
     *p = static_cast<P*>(q);
     return MG_OK;
@@ -542,6 +570,10 @@ inline Cycle vcycle_of(const mg_handle* h) {
 // preconditioner, so x^(1) = 0 as well).
 template <typename T, typename C, typename B, typename O>
 mg_status mgv(mg_handle* h, const Cycle& cy, int l, const B* b, O* out, cudaStream_t s) {
+    static const char* const level_range[MG_MAX_LEVELS] = {"V-cycle level 0", "V-cycle level 1", "V-cycle level 2",
+                                                           "V-cycle level 3", "V-cycle level 4", "V-cycle level 5",
+                                                           "V-cycle level 6", "V-cycle level 7"};
+    NvtxRange nvtx_(level_range[l]);   // the level and the levels below it (nested ranges)
     typedef View<T, C> V;
     DevLevel& d = h->lv[l];
     const Lvl<T, C> L = V::lvl(h, l);
@@ -1425,8 +1457,8 @@ mg_status setup_impl(mg_handle* h, const mg_mesh* mesh, const mg_params* prm, co
     TRY(dalloc(h, &h->tickets, TK_COUNT));
     CK(cudaMemset(h->tickets, 0, TK_COUNT * sizeof(unsigned int)));
     CK(cudaMemset(h->gs, 0, sizeof(mg::GcrScal)));
-    if (cudaMallocHost(&h->host_sc, 4 * sizeof(double)) != cudaSuccess) return MG_ERR_NOMEM;
-    if (cudaMallocHost(&h->host_bs, sizeof(mg::BicgScal)) != cudaSuccess) return MG_ERR_NOMEM;
+    if (!mem_alloc((void**)&h->host_sc, 4 * sizeof(double), MEM_PINNED)) return MG_ERR_NOMEM;
+    if (!mem_alloc((void**)&h->host_bs, sizeof(mg::BicgScal), MEM_PINNED)) return MG_ERR_NOMEM;
     TRY(dalloc(h, &h->bs, 1));
     CK(cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking));
     CK(cudaStreamCreateWithFlags(&h->run, cudaStreamNonBlocking));
@@ -1439,9 +1471,9 @@ mg_status setup_impl(mg_handle* h, const mg_mesh* mesh, const mg_params* prm, co
 
 void free_handle(mg_handle* h) {
     if (!h) return;
-    for (void* p : h->allocs) cudaFree(p);
-    if (h->host_sc) cudaFreeHost(h->host_sc);
-    if (h->host_bs) cudaFreeHost(h->host_bs);
+    for (void* p : h->allocs) mem_free(p, MEM_DEVICE);
+    mem_free(h->host_sc, MEM_PINNED);
+    mem_free(h->host_bs, MEM_PINNED);
     for (auto& row : h->gexec)
         for (cudaGraphExec_t g : row)
             if (g) cudaGraphExecDestroy(g);
@@ -1476,10 +1508,10 @@ void free_ensemble(mg_ensemble* e) {
     if (!e) return;
     if (e->exec) cudaGraphExecDestroy(e->exec);
     if (e->graph) cudaGraphDestroy(e->graph);
-    if (e->st) cudaFree(e->st);
-    if (e->host_st) cudaFreeHost(e->host_st);
-    if (e->stamps) cudaFree(e->stamps);
-    if (e->host_stamps) cudaFreeHost(e->host_stamps);
+    mem_free(e->st, MEM_DEVICE);
+    mem_free(e->host_st, MEM_PINNED);
+    mem_free(e->stamps, MEM_DEVICE);
+    mem_free(e->host_stamps, MEM_PINNED);
     if (e->cs) cudaStreamDestroy(e->cs);
     delete e;
 }
@@ -1565,13 +1597,11 @@ mg_status build_member(mg_ensemble* e, int i, mg_handle* h, const double* b, dou
 
 mg_status build_ensemble(mg_ensemble* e, const double* const* b, double* const* x, double tol) {
     CK(cudaStreamCreateWithFlags(&e->cs, cudaStreamNonBlocking));
-    if (cudaMalloc(&e->st, e->count * sizeof(mg::EnsState)) != cudaSuccess ||
-        cudaMallocHost(&e->host_st, e->count * sizeof(mg::EnsState)) != cudaSuccess ||
-        cudaMalloc(&e->stamps, (e->count + 1) * sizeof(unsigned long long)) != cudaSuccess ||
-        cudaMallocHost(&e->host_stamps, (e->count + 1) * sizeof(unsigned long long)) != cudaSuccess) {
-        cudaGetLastError();
+    if (!mem_alloc((void**)&e->st, e->count * sizeof(mg::EnsState), MEM_DEVICE) ||
+        !mem_alloc((void**)&e->host_st, e->count * sizeof(mg::EnsState), MEM_PINNED) ||
+        !mem_alloc((void**)&e->stamps, (e->count + 1) * sizeof(unsigned long long), MEM_DEVICE) ||
+        !mem_alloc((void**)&e->host_stamps, (e->count + 1) * sizeof(unsigned long long), MEM_PINNED))
         return MG_ERR_NOMEM;
-    }
     CK(cudaGraphCreate(&e->graph, 0));
     // root: the launch time; every member starts after it
     std::vector<cudaGraphNode_t> root, deps;
@@ -1601,6 +1631,14 @@ extern "C" {
 const char* mg_last_cuda_error(void) {
     return g_last_cuda == cudaSuccess ? "no CUDA error" : cudaGetErrorName(g_last_cuda);
 }
+
+int64_t mg_inject_alloc_failure(int64_t nth) {
+    const long long seen = g_alloc_seen.exchange(0);
+    g_fail_at.store(nth > 0 ? nth : 0);
+    return seen;
+}
+
+int64_t mg_live_allocations(void) { return g_live.load(); }
 
 const char* mg_status_string(mg_status s) {
     switch (s) {
@@ -1685,8 +1723,7 @@ mg_status mg_setup_coeffs(const mg_mesh* mesh, const mg_params* prm, const doubl
     const size_t n6 = 6 * cells(h, 0);
     double* tmp = nullptr;
     mg_status st = MG_OK;
-    if (cudaMalloc(&tmp, n6 * sizeof(double)) != cudaSuccess) {
-        cudaGetLastError();
+    if (!mem_alloc((void**)&tmp, n6 * sizeof(double), MEM_DEVICE)) {
         st = MG_ERR_NOMEM;
     } else if (cudaMemcpy(tmp, coeffs, n6 * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess) {
         st = MG_ERR_CUDA;
@@ -1694,7 +1731,7 @@ mg_status mg_setup_coeffs(const mg_mesh* mesh, const mg_params* prm, const doubl
         st = set_coefficients_impl(h, tmp, nullptr);
         if (st == MG_OK && cudaDeviceSynchronize() != cudaSuccess) st = MG_ERR_CUDA;
     }
-    if (tmp) cudaFree(tmp);
+    mem_free(tmp, MEM_DEVICE);
     if (st != MG_OK) {
         mg_destroy(h);
         return st;

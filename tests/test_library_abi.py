@@ -50,6 +50,15 @@ def test_precision_constants_match_the_header():
     assert set(mg.PRECISIONS.values()) == {0, 1, 2, 3}
 
 
+def test_allocation_failure_hook_counts_attempts(lib):
+    """The injection hook is inert until armed and counts attempted allocations (none here: no
+    set-up reaches the device without a GPU); no allocation is live."""
+    assert lib.mg_inject_alloc_failure(0) >= 0
+    assert lib.mg_inject_alloc_failure(3) == 0
+    assert lib.mg_inject_alloc_failure(0) == 0
+    assert lib.mg_live_allocations() >= 0
+
+
 def _setup_raw(lib, n=4, nlev=3, levels=2, precision=0, restart=5, max_iter=10, n_coarse=4, g=None,
                null_mesh=False, mixed=None):
     import paper_2002_00756_gb300 as mg
