@@ -31,6 +31,7 @@ MEMBERS = [  # (config, precision, max_iter, rhs scale)
     (syn.small_config(20, 9, levels=3, seed=syn.BASE_SEED + 32), "fp32_bf16", 200, 1.0),
     (syn.small_config(8, 30, levels=3, seed=syn.BASE_SEED + 33), "fp32", 200, 0.0),
     (syn.small_config(24, 12, levels=4, seed=syn.BASE_SEED + 34), "fp32", 2, 1.0),
+    (syn.small_config(16, 10, levels=3, seed=syn.BASE_SEED + 36), "fp32_p64", 200, 1.0),
 ]
 
 
